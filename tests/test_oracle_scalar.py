@@ -1,0 +1,385 @@
+"""Pins of the scalar oracle against what the paper and mathematics fix.
+
+Each test checks the oracle (oracle/fqnm_oracle.c) against something other
+than itself: exact rational arithmetic, brute force over every state of tiny
+problems, exact invariants (telescoping conservation), closed-form special
+cases, the monotone-scheme properties of the Lemma on CFL stability where the
+rounded maps keep the scheme monotone, Theorem (transfer-operator
+equivalence), and the O(delta) bound of Proposition (update-level
+correspondence).
+"""
+import itertools
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2604_06947_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FACTS = json.load(open(os.path.join(HERE, "golden", "paper_facts.json")))
+
+
+# ---------------------------------------------------------------------------
+# exact rational transfer maps, eq. flux_table
+# ---------------------------------------------------------------------------
+
+def exact_split(kind, sign, u, a, alpha):
+    if kind == "linear_upwind":
+        return (max(a, 0) if sign > 0 else min(a, 0)) * u
+    if kind == "linear_lf":
+        return Fraction(1, 2) * (a * u + sign * alpha * u)
+    if kind == "burgers_lf":
+        return Fraction(1, 2) * (Fraction(1, 2) * u * u + sign * alpha * u)
+    if kind == "burgers_eo":
+        w = max(u, 0) if sign > 0 else min(u, 0)
+        return Fraction(1, 2) * w * w
+    raise ValueError(kind)
+
+
+def exact_phi(kind, sign, q, delta, dx, dt, a=0.0, alpha=0.0):
+    """round(f(delta q) dt/dx / delta) in exact rationals; Python's round()
+    of a Fraction is round-half-to-even.  Returns (phi, exact value)."""
+    d = Fraction(delta)
+    lam = Fraction(dt) / Fraction(dx)
+    v = exact_split(kind, sign, d * q, Fraction(a), Fraction(alpha)) * lam / d
+    return round(v), v
+
+
+def near_tie(v, rel=2.0 ** -40):
+    frac = v - (v.numerator // v.denominator)
+    return abs(frac - Fraction(1, 2)) <= rel * max(1, abs(v))
+
+
+CASES = [
+    # (name, kind, delta, dx, dt, a, alpha, lo, hi)
+    ("cfg0_upwind_nu0.5", "linear_upwind", 2.0 ** -12, 1 / 1024, 0.5 / 1024, 1.0, 0.0, -1100, 5200),
+    ("cfg2_upwind_nu0.9_low", "linear_upwind", 2.0 ** -20, 2.0 ** -24, 0.9 * 2.0 ** -24, 1.0, 0.0, 0, 3000),
+    ("cfg2_upwind_nu0.9_high", "linear_upwind", 2.0 ** -20, 2.0 ** -24, 0.9 * 2.0 ** -24, 1.0, 0.0, 2 ** 21 - 3000, 2 ** 21),
+    ("cfg1_burgers_low", "burgers_lf", 2.0 ** -16, 2.0 ** -20, 0.4 * 2.0 ** -20 / 1.3, 0.0, 1.3, -20000, -18500),
+    ("cfg1_burgers_mid", "burgers_lf", 2.0 ** -16, 2.0 ** -20, 0.4 * 2.0 ** -20 / 1.3, 0.0, 1.3, -600, 600),
+    ("cfg1_burgers_high", "burgers_lf", 2.0 ** -16, 2.0 ** -20, 0.4 * 2.0 ** -20 / 1.3, 0.0, 1.3, 84000, 85300),
+    ("linear_lf_neg_a", "linear_lf", 2.0 ** -10, 1 / 512, 0.3 / 512, -0.7, 0.9, -900, 900),
+    ("burgers_eo", "burgers_eo", 2.0 ** -10, 1 / 512, 0.5 / 512, 0.0, 0.0, -900, 900),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_tables_match_exact_rationals(orc, case):
+    name, kind, delta, dx, dt, a, alpha, lo, hi = case
+    p, m = orc.split_table(kind, delta, dx, dt, lo, hi - lo + 1, a=a, alpha=alpha)
+    mismatches = []
+    for k, q in enumerate(range(lo, hi + 1)):
+        for sign, got in ((+1, p[k]), (-1, m[k])):
+            want, v = exact_phi(kind, sign, q, delta, dx, dt, a, alpha)
+            if got != want:
+                # only FP64 double rounding next to a .5 tie may differ
+                assert near_tie(v), (name, q, sign, got, want, float(v))
+                assert abs(got - want) == 1
+                mismatches.append(q)
+    # the epsilon of the proof of Proposition (update-level correspondence)
+    lam = Fraction(dt) / Fraction(dx)
+    eps_max = FACTS["eps_bound"]["value"]
+    for q in range(lo, hi + 1, max(1, (hi - lo) // 200)):
+        for sign, tab in ((+1, p), (-1, m)):
+            _, v = exact_phi(kind, sign, q, delta, dx, dt, a, alpha)
+            assert abs(tab[q - lo] - v) <= eps_max + Fraction(1, 2 ** 30)
+    if name.startswith("cfg2"):
+        # q*0.9 in double lands on an exact .5 tie whenever q = 5 (mod 10):
+        # the rounding mode is part of the contract (half-even, reading R1)
+        assert len(mismatches) > 0
+
+
+def test_cfg0_table_is_half_even_halving(orc):
+    lo, hi = -1024, 5120
+    p, m = orc.split_table("linear_upwind", 2.0 ** -12, 1 / 1024, 0.5 / 1024,
+                           lo, hi - lo + 1, a=1.0)
+    q = np.arange(lo, hi + 1)
+    assert np.array_equal(p, np.array([round(Fraction(int(x), 2)) for x in q]))
+    assert not m.any()
+
+
+@pytest.mark.parametrize("rounding", ["half_even", "half_away", "floor"])
+def test_rounding_modes_keep_maps_monotone(orc, rounding):
+    """Step 1 of the proof of the Lemma on CFL stability: phi+ nondecreasing,
+    phi- nonincreasing, for every rounding mode, on states where the LF
+    bound alpha >= |f'(u)| holds (|u| <= 1.3 = 5324.8 quanta of 2^-12)."""
+    for kind, a, alpha in (("burgers_lf", 0.0, 1.3), ("linear_lf", 0.6, 1.0),
+                           ("linear_upwind", -1.0, 0.0)):
+        p, m = orc.split_table(kind, 2.0 ** -12, 2.0 ** -10, 0.4 * 2.0 ** -10 / 1.3,
+                               -5324, 10649, a=a, alpha=alpha, rounding=rounding)
+        assert np.all(np.diff(p) >= 0) and np.all(np.diff(m) <= 0)
+
+
+def test_rounding_modes_differ_only_at_ties(orc):
+    lo, cnt = -64, 129
+    args = ("linear_upwind", 2.0 ** -4, 1.0, 0.5)
+    he, _ = orc.split_table(*args, lo, cnt, a=1.0, rounding="half_even")
+    ha, _ = orc.split_table(*args, lo, cnt, a=1.0, rounding="half_away")
+    fl, _ = orc.split_table(*args, lo, cnt, a=1.0, rounding="floor")
+    q = np.arange(lo, lo + cnt)
+    assert np.array_equal(fl, q // 2)
+    assert np.array_equal(ha, np.sign(q) * ((np.abs(q) + 1) // 2))
+    odd = (q % 2) != 0
+    assert np.array_equal(he[~odd], ha[~odd])
+
+
+# ---------------------------------------------------------------------------
+# the update, eq. update_rule
+# ---------------------------------------------------------------------------
+
+def small_params():
+    # coarse quantum so that the maps are non-trivial on q in [0, 8]
+    return dict(delta=0.125, dx=0.25, dt=0.1875)     # lambda = 0.75
+
+
+def python_face_step(q, tab_p, tab_m, boundary="periodic"):
+    """Pairwise exchange across each face (an independent organisation)."""
+    n = len(q)
+    new = list(q)
+    faces = n if boundary == "periodic" else n - 1
+    for f in range(faces):
+        L, R = f, (f + 1) % n
+        F = tab_p[q[L]] + tab_m[q[R]]
+        new[L] -= F
+        new[R] += F
+    if boundary == "transmissive":
+        new[0] += tab_p[q[0]] + tab_m[q[0]]
+        new[n - 1] -= tab_p[q[n - 1]] + tab_m[q[n - 1]]
+    return new
+
+
+@pytest.mark.parametrize("kind,a,alpha", [("linear_upwind", 1.0, 0.0),
+                                          ("burgers_lf", 0.0, 1.0),
+                                          ("linear_lf", -0.5, 1.0)])
+def test_brute_force_all_states(orc, kind, a, alpha):
+    """Every state of q in [0,8]^N, N = 2..4, two steps, against exact-rational
+    maps driven by a pure-Python face loop."""
+    sp = small_params()
+    tab = {}
+    for q in range(-64, 80):
+        tab[q] = (exact_phi(kind, +1, q, sp["delta"], sp["dx"], sp["dt"], a, alpha)[0],
+                  exact_phi(kind, -1, q, sp["delta"], sp["dx"], sp["dt"], a, alpha)[0])
+    tp = {k: v[0] for k, v in tab.items()}
+    tm = {k: v[1] for k, v in tab.items()}
+    for n in (2, 3, 4):
+        for bnd in ("periodic", "transmissive"):
+            for state in itertools.product(range(9), repeat=n):
+                want = python_face_step(list(state), tp, tm, bnd)
+                want = python_face_step(want, tp, tm, bnd)
+                got = orc.step(np.array(state), kind, steps=2, a=a, alpha=alpha,
+                               boundary=bnd, **sp)
+                assert list(got) == want, (n, bnd, state)
+
+
+@pytest.mark.parametrize("boundary", ["periodic", "transmissive"])
+@pytest.mark.parametrize("kind,a,alpha", [("burgers_lf", 0.0, 1.3),
+                                          ("linear_upwind", 1.0, 0.0),
+                                          ("linear_lf", -0.8, 1.1)])
+def test_cell_form_equals_face_form(orc, kind, a, alpha, boundary):
+    p = I.burgers_problem(n=1537, steps=0)
+    q0 = orc.quantise(p.u0, 2.0 ** -12)
+    kw = dict(delta=2.0 ** -12, dx=p.dx, dt=0.45 * p.dx / 1.3, a=a, alpha=alpha,
+              boundary=boundary)
+    c = orc.step(q0, kind, steps=60, **kw)
+    f = orc.step_faces(q0, kind, steps=60, **kw)
+    assert np.array_equal(c, f)
+
+
+def test_exact_conservation_every_step(orc):
+    """eq. exact_conservation: sum(q) is the same integer after every step;
+    for a transmissive domain it changes by exactly the boundary transfer."""
+    p = I.burgers_problem(n=4096, steps=0)
+    q = orc.quantise(p.u0, p.delta)
+    m0 = int(q.sum())
+    for _ in range(300):
+        q = orc.step(q, "burgers_lf", p.delta, p.dx, p.dt, 1, alpha=p.alpha)
+        assert int(q.sum()) == m0
+    q = orc.quantise(p.u0, p.delta)
+    qt, bf = orc.step(q, "burgers_lf", p.delta, p.dx, p.dt, 300, alpha=p.alpha,
+                      boundary="transmissive", return_bflux=True)
+    assert bf != 0 and int(qt.sum()) == m0 - bf
+
+
+def test_aggregated_mass_is_conserved(orc):
+    """Coarse observation by block sums sees the same invariant total."""
+    p = I.burgers_problem(n=4096, steps=0)
+    q = orc.quantise(p.u0, p.delta)
+    q1 = orc.step(q, "burgers_lf", p.delta, p.dx, p.dt, 500, alpha=p.alpha)
+    assert q1.reshape(64, 64).sum(axis=1).sum() == q.sum()
+
+
+def test_unit_courant_upwind_is_exact_shift(orc):
+    """nu = 1, upwind: phi+(q) = q, so q_i^{n+1} = q_{i-1}^n and N steps give
+    back the initial state."""
+    n = 777
+    rng = np.random.default_rng(3)
+    q0 = rng.integers(-10 ** 6, 10 ** 6, n)
+    q1 = orc.step(q0, "linear_upwind", 2.0 ** -20, 1.0 / n, 1.0 / n, 1, a=1.0)
+    assert np.array_equal(q1, np.roll(q0, 1))
+    qN = orc.step(q0, "linear_upwind", 2.0 ** -20, 1.0 / n, 1.0 / n, n, a=1.0)
+    assert np.array_equal(qN, q0)
+
+
+def test_constant_state_is_stationary(orc):
+    for kind, a, alpha in (("burgers_lf", 0.0, 1.3), ("linear_upwind", 1.0, 0.0)):
+        q = np.full(100, 12345, dtype=np.int64)
+        assert np.array_equal(orc.step(q, kind, 2.0 ** -16, 0.01, 0.003, 50,
+                                       a=a, alpha=alpha), q)
+
+
+def certificate(orc, kind, delta, dx, dt, lo, hi, a=0.0, alpha=0.0):
+    """H(q) = q - phi+(q) + phi-(q) nondecreasing on [lo, hi]: with phi+
+    nondecreasing and phi- nonincreasing this makes the integer update
+    monotone in all three arguments."""
+    p, m = orc.split_table(kind, delta, dx, dt, lo, hi - lo + 1, a=a, alpha=alpha)
+    H = np.arange(lo, hi + 1) - p + m
+    return bool(np.all(np.diff(H) >= 0))
+
+
+@pytest.mark.parametrize("nu", [0.5, 0.9, 1.0])
+def test_monotone_scheme_properties_upwind(orc, nu):
+    """Lemma on CFL stability (i)-(iii) and order preservation, exactly, where
+    the rounded maps keep the scheme monotone (the certificate holds)."""
+    n, delta = 600, 2.0 ** -14
+    dx, dt = 1.0 / n, nu / n
+    rng = np.random.default_rng(int(nu * 10))
+    q = rng.integers(0, 2 ** 15, n)
+    qt = q + rng.integers(0, 50, n)          # ordered: q <= qt
+    assert certificate(orc, "linear_upwind", delta, dx, dt, -10, 2 ** 15 + 60, a=1.0)
+    inv = orc.invariants
+    for _ in range(40):
+        q1 = orc.step(q, "linear_upwind", delta, dx, dt, 1, a=1.0)
+        qt1 = orc.step(qt, "linear_upwind", delta, dx, dt, 1, a=1.0)
+        assert q1.min() >= q.min() and q1.max() <= q.max()           # (i)
+        assert inv(q1)[1] <= inv(q)[1]                                # (ii)
+        assert inv(q1, qt1)[2] <= inv(q, qt)[2]                       # (iii)
+        assert np.all(q1 <= qt1)                                       # order
+        q, qt = q1, qt1
+
+
+def test_burgers_lf_split_rounding_deviation_is_small(orc):
+    """With split rounding the LF Burgers maps are not everywhere monotone in
+    the centre cell (H decreases at some levels), so the Lemma's max
+    principle can fail by a few quanta.  Measured, bounded, and mass exact."""
+    p = I.burgers_problem(n=4096, steps=0)
+    q = orc.quantise(p.u0, p.delta)
+    assert not certificate(orc, "burgers_lf", p.delta, p.dx, p.dt,
+                           int(q.min()), int(q.max()), alpha=p.alpha)
+    lo, hi = q.min(), q.max()
+    worst = 0
+    for _ in range(50):
+        q = orc.step(q, "burgers_lf", p.delta, p.dx, p.dt, 20, alpha=p.alpha)
+        worst = max(worst, int(lo - q.min()), int(q.max() - hi))
+    assert worst <= 16
+
+
+def test_cone_matches_full_run(orc):
+    p = I.burgers_problem(n=2048, steps=0)
+    q0 = orc.quantise(p.u0, p.delta)
+    full = orc.step(q0, "burgers_lf", p.delta, p.dx, p.dt, 300, alpha=p.alpha)
+    for i in (0, 5, 1000, 2047):
+        assert orc.cone(q0, i, 300, "burgers_lf", p.delta, p.dx, p.dt,
+                        alpha=p.alpha) == full[i]
+
+
+# ---------------------------------------------------------------------------
+# Theorem (transfer-operator equivalence) and its remark on collapse
+# ---------------------------------------------------------------------------
+
+def test_collapse_lf_at_speed_equals_upwind(orc):
+    p = I.linear_advection_problem(n=512, steps=0)
+    q0 = orc.quantise(p.u0, p.delta)
+    tu = orc.split_table("linear_upwind", p.delta, p.dx, p.dt, -2000, 8000, a=1.0)
+    tl = orc.split_table("linear_lf", p.delta, p.dx, p.dt, -2000, 8000, a=1.0, alpha=1.0)
+    assert np.array_equal(tu[0], tl[0]) and np.array_equal(tu[1], tl[1])
+    a = orc.step(q0, "linear_upwind", p.delta, p.dx, p.dt, 700, a=1.0)
+    b = orc.step(q0, "linear_lf", p.delta, p.dx, p.dt, 700, a=1.0, alpha=1.0)
+    assert np.array_equal(a, b)
+
+
+def test_collapse_burgers_fluxes_on_positive_states(orc):
+    """On positive states Godunov, Engquist-Osher and the upwind flux f(uL)
+    induce the same two-point transfer, hence identical trajectories."""
+    n, delta = 512, 2.0 ** -12
+    x = I.cell_centres(n)
+    u = 0.7 + 0.5 * np.sin(2 * np.pi * x)          # in [0.2, 1.2]
+    q0 = orc.quantise(u, delta)
+    dx, dt = 1.0 / n, 0.4 / n / 1.2
+    for qL, qR in ((900, 4000), (4000, 900), (3000, 3000), (820, 821)):
+        g = orc.two_point_phi("burgers_godunov", delta, dx, dt, qL, qR)
+        e = orc.two_point_phi("burgers_eo", delta, dx, dt, qL, qR)
+        assert g == e
+    a = orc.step_two_point(q0, "burgers_godunov", delta, dx, dt, 400)
+    b = orc.step_two_point(q0, "burgers_eo", delta, dx, dt, 400)
+    c = orc.step(q0, "burgers_eo", delta, dx, dt, 400)     # split form, phi- = 0
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert not np.array_equal(a, q0)
+
+
+def test_collapse_under_flux_perturbation_and_negative_control(orc):
+    p = I.burgers_problem(n=2048, steps=0)
+    q0 = orc.quantise(p.u0, p.delta)
+    lo, hi = int(q0.min()) - 64, int(q0.max()) + 64
+    base = orc.split_table("burgers_lf", p.delta, p.dx, p.dt, lo, hi - lo + 1, alpha=1.3)
+    near = orc.split_table("burgers_lf", p.delta, p.dx, p.dt, lo, hi - lo + 1,
+                           alpha=1.3 * (1 + 2.0 ** -45))
+    far = orc.split_table("burgers_lf", p.delta, p.dx, p.dt, lo, hi - lo + 1, alpha=1.5)
+    same = np.array_equal(base[0], near[0]) and np.array_equal(base[1], near[1])
+    a = orc.step(q0, "burgers_lf", p.delta, p.dx, p.dt, 500, alpha=1.3)
+    b = orc.step(q0, "burgers_lf", p.delta, p.dx, p.dt, 500, alpha=1.3 * (1 + 2.0 ** -45))
+    if same:                      # condition of the theorem holds on the range
+        assert np.array_equal(a, b)
+    assert not np.array_equal(base[0], far[0])
+    c = orc.step(q0, "burgers_lf", p.delta, p.dx, p.dt, 500, alpha=1.5)
+    assert not np.array_equal(a, c)
+
+
+# ---------------------------------------------------------------------------
+# Proposition (update-level correspondence with the classical split scheme)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,a,alpha", [("burgers_lf", 0.0, 1.3),
+                                          ("linear_upwind", 1.0, 0.0)])
+def test_one_step_increment_within_two_quanta_of_fv(orc, kind, a, alpha):
+    p = I.burgers_problem(n=8192, steps=0)
+    delta = 2.0 ** -16
+    q = orc.quantise(p.u0, delta)
+    u = delta * q.astype(np.float64)
+    q1 = orc.step(q, kind, delta, p.dx, p.dt, 1, a=a, alpha=alpha)
+    u1 = orc.fv_step(u, kind, p.dx, p.dt, 1, a=a, alpha=alpha)
+    d_int = delta * (q1 - q).astype(np.float64)
+    d_fv = u1 - u
+    err = np.abs(d_int - d_fv)
+    assert err.max() <= 2 * delta * (1 + 1e-9)
+    assert err.max() > 0
+
+
+def test_fqnm_tracks_fv_over_many_steps(orc):
+    """||u_FQNM - u_FV||_1 (dx-weighted) <= delta/2 + 2 n delta for the
+    monotone linear case."""
+    p = I.linear_advection_problem(n=1024, steps=0)
+    q0 = orc.quantise(p.u0, p.delta)
+    u0 = p.delta * q0.astype(np.float64)
+    for n_steps in (10, 100, 400):
+        q = orc.step(q0, "linear_upwind", p.delta, p.dx, p.dt, n_steps, a=1.0)
+        u = orc.fv_step(u0, "linear_upwind", p.dx, p.dt, n_steps, a=1.0)
+        l1 = p.dx * np.abs(p.delta * q - u).sum()
+        assert l1 <= p.delta / 2 + 2 * n_steps * p.delta
+
+
+# ---------------------------------------------------------------------------
+# Supplementary: level entropy
+# ---------------------------------------------------------------------------
+
+def test_level_entropy_log_count(orc):
+    """Proposition (log-count structure): uniform occupation of m levels gives
+    S = log m; one level gives 0."""
+    for m in (1, 2, 7, 64):
+        q = np.repeat(np.arange(m) * 3 - 5, 11)
+        assert abs(orc.level_entropy(q) - np.log(m)) < 1e-12
+    q = np.array([0, 0, 0, 1])
+    want = -(0.75 * np.log(0.75) + 0.25 * np.log(0.25))
+    assert abs(orc.level_entropy(q) - want) < 1e-15
