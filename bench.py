@@ -1,0 +1,381 @@
+"""Throughput of the FQNM quantised conservative step on GB300.
+
+Workload (one bench "step" = one whole problem through the hot path):
+inviscid Burgers, LF split flux (alpha = 1.3), periodic, N = 2^20 cells,
+delta = 2^-16, Courant number 0.4, 10^4 time steps from the seeded
+random-steps initial field:
+    quantise u0 -> build and verify the transfer rule -> 10^4 steps of the
+    integer update -> observable -> exact invariants.
+Metric: cell updates per second (bit-exact integer states).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fqnm|reference]
+
+N > 1 runs under torchrun: one process per GPU, each solving its own problem
+(independent problems, weak scaling, no data-path collective); the time is
+the maximum over ranks.  --impl reference times the CPU oracle (the plain
+single-threaded implementation the tests check against) on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_06947_gb300 import inputs as I  # noqa: E402
+
+METRIC = "cell-updates/s"
+UNIT = "cell-updates/s"
+BYTES_PER_UPDATE = 8          # int32 read + int32 write per cell per step
+FALLBACK_HBM_GBS = 6800.0
+CPU_SAMPLE_STEPS = 3000       # oracle sample: 2^20 cells x 3000 steps
+REF_SAMPLE_STEPS = 100        # --impl reference: per bench step
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(kernel_tag: str, src_digest: str):
+    """Bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        for line in open(path):
+            f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+            if f.get("kernel") == kernel_tag and f.get("src_sha") == src_digest:
+                return float(f["dram_bytes_per_launch"])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_2604_06947_gb300 import fqnm as F
+    from paper_2604_06947_gb300 import build as B
+
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F.load()
+
+    p = I.burgers_problem(seed=I.BASE_SEED + 1 + rank)      # one problem per rank
+    n, T = p.n, p.steps
+    stream = torch.cuda.Stream()
+    u0_dev = torch.from_numpy(p.u0).to(dev)
+    u_out = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    s = F.Solver.for_problem(p, autotune=1)
+    F.fqnm_set_stream(s.h, stream)
+    s.n = n
+
+    def one_step(ev=None):
+        """quantise+load (rule build), T steps, observe, invariants."""
+        F.fqnm_load_field(s.h, u0_dev, n, on_device=True)
+        if ev is not None:
+            ev[0].record(stream)
+        F.fqnm_step(s.h, T)
+        if ev is not None:
+            ev[1].record(stream)
+        F.fqnm_observe_device(s.h, u_out)
+        return F.fqnm_invariants(s.h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            inv = one_step()
+    mass0 = inv["mass"][0]
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = F.fqnm_kernel_launches()
+    step_ms, region_ms = [], []
+    step_launches = 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()                                   # evict L2 between steps
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ra, rb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            inv = one_step((ra, rb))
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            region_ms.append(ra.elapsed_time(rb))
+            step_launches += F.fqnm_get_stats(s.h)["launches"]   # reset by each load
+            assert inv["mass"][0] == mass0, "mass not conserved"
+    torch.cuda.synchronize()
+    launches = F.fqnm_kernel_launches() - launches0
+    stats = F.fqnm_get_stats(s.h)
+    clk = clocks.stop()
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = n * T * args.steps * world
+    value = updates / (total_ms / 1e3)
+
+    # dominant kernel: the temporal-blocked step, launched only inside the
+    # stepping region; average launch duration from the events around it
+    avg_launch_s = (sum(region_ms) / 1e3) / max(step_launches, 1)
+    bytes_per_launch = BYTES_PER_UPDATE * n * (T * args.steps) / max(step_launches, 1)
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = measured_peak()
+    kernel_tag = "k_step_tb:L%d:V%d" % (stats["layout"], stats["cells_per_thread"])
+    traffic = profiled_traffic(kernel_tag, B.source_digest())
+
+    # end to end through the C ABI with host buffers (rank-local)
+    u0_host = torch.from_numpy(p.u0).pin_memory()
+    u_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    lib = F.load()
+    for i in range(max(2, args.steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F._check(lib.fqnm_load_field(s.h, u0_host.data_ptr(), n, 0))
+        F.fqnm_step(s.h, T)
+        F._check(lib.fqnm_observe(s.h, u_host.data_ptr()))
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_times.append(t1 - t0)
+    e2e_value = n * T / statistics.median(e2e_times) * world
+
+    result = None
+    if rank == 0:
+        baselines = fv_baselines(F, p, stream, torch) if not args.no_fv else None
+        cpu = cpu_baseline(p) if (world == 1 and not args.no_cpu) else None
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "burgers_lf_1m_cells_10k_steps", "n_cells": n,
+                       "time_steps_per_step": T, "delta": "2^-16", "courant": 0.4,
+                       "alpha": p.alpha, "flux": "burgers_lf", "boundary": "periodic",
+                       "seed": I.BASE_SEED + 1, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
+                       "plan": {"kernel": "k_step_tb", "layout": stats["layout"],
+                                "cells_per_thread": stats["cells_per_thread"],
+                                "block": stats["block"], "k": stats["k"],
+                                "graph": stats["graph"]}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind,
+                         "kernel": kernel_tag,
+                         "bytes_model": "8 B per cell update (int32 read + write), "
+                                        "x cells x steps per launch; effective under "
+                                        "temporal blocking"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if cpu:
+            result["cpu_baseline"] = cpu
+        if baselines:
+            result["fv_baseline"] = baselines
+        print(json.dumps(result))
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def fv_baselines(F, p, stream, torch):
+    """FP32 / FP64 finite-volume baseline with the same split flux on the same
+    GPU (one step per launch), its throughput and its L1 distance to FQNM."""
+    steps = 2000
+    n = p.n
+    q0 = F.fqnm_quantise(p.u0, p.delta)
+    u0 = p.delta * q0.astype(np.float64)
+    s = F.Solver.for_problem(p, autotune=1)
+    s.load(q0).step(steps)
+    u_int = s.observe()
+    s.close()
+    out = {"time_steps": steps}
+    for prec in (32, 64):
+        h = F.fqnm_fv_create(F.make_flux(p.flux, alpha=p.alpha), p.dx, p.dt, "periodic", prec)
+        F.fqnm_fv_set_stream(h, stream)
+        F.fqnm_fv_load(h, u0)
+        F.fqnm_fv_step(h, 50)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        F.fqnm_fv_load(h, u0)
+        a.record(stream)
+        F.fqnm_fv_step(h, steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        u = F.fqnm_fv_observe(h, n)
+        F.fqnm_fv_destroy(h)
+        out["fp%d" % prec] = {"value": n * steps / (ms / 1e3), "unit": UNIT,
+                              "l1_vs_fqnm": float(p.dx * np.abs(u - u_int).sum())}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(p, steps: int = CPU_SAMPLE_STEPS):
+    from oracle import oracle as O
+    q0 = O.quantise(p.u0, p.delta)
+    t0 = time.perf_counter()
+    O.step(q0, p.flux, p.delta, p.dx, p.dt, steps, alpha=p.alpha)
+    dt = time.perf_counter() - t0
+    return {"value": p.n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d cells x %d of the 10^4 time steps (same seeded problem), "
+                      "single-threaded C oracle, %.1f s" % (p.n, steps, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    p = I.burgers_problem()
+    q0 = O.quantise(p.u0, p.delta)
+    for _ in range(args.warmup):
+        O.step(q0, p.flux, p.delta, p.dx, p.dt, 10, alpha=p.alpha)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.step(q0, p.flux, p.delta, p.dx, p.dt, REF_SAMPLE_STEPS, alpha=p.alpha)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = p.n * REF_SAMPLE_STEPS * args.steps / total
+    res = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "burgers_lf_1m_cells_10k_steps", "n_cells": p.n,
+                   "time_steps_per_step": REF_SAMPLE_STEPS,
+                   "note": "each step is a bounded sample (%d of the 10^4 time steps)"
+                           % REF_SAMPLE_STEPS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d cells x %d time steps per bench step"
+                                   % (p.n, REF_SAMPLE_STEPS)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res))
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fqnm", choices=["fqnm", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fv", action="store_true", help="skip the FP finite-volume baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

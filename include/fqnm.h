@@ -1,0 +1,262 @@
+/*
+ * fqnm.h -- C ABI of libfqnm, the GB300 (sm_103a) implementation of the
+ * quantised conservative step of the Fast Quantised Numerical Method
+ * (Park, Ha & Kang, arXiv 2604.06947).
+ *
+ * The method (§2, eqs. quantisation, flux_table, update_rule):
+ *   q_i = round(u_i / delta)                       integer state
+ *   phi+-(q) = round(f+-(delta q) dt/dx / delta)   integer transfer maps
+ *   F_{i+1/2} = phi+(q_i) + phi-(q_{i+1})          face count flux
+ *   q_i <- q_i - (F_{i+1/2} - F_{i-1/2})           telescoping update
+ *   u_i = delta q_i                                observable, on request
+ *
+ * Conventions for every call:
+ *   - Every call returns an fqnm_status; no call aborts, traps or exits.
+ *     On failure fqnm_last_error() holds a message (thread-local).
+ *   - A handle is not thread-safe: use one handle per host thread.
+ *   - "host" pointers are ordinary CPU memory owned by the caller; the call
+ *     copies what it needs before returning.  "device" pointers are CUDA
+ *     global memory owned by the caller (for example a torch tensor); the
+ *     call only reads or writes them, in stream order on the handle's stream.
+ *   - Device memory of a handle belongs to the library and is released by
+ *     the matching destroy call.
+ *   - Steps are enqueued asynchronously on the handle's stream; errors of the
+ *     device work (a state leaving the verified range of the transfer map)
+ *     surface at the next synchronising call (sync, observe, checkpoint,
+ *     invariants).
+ *   - delta must be a power of two (so delta*q and v/delta are exact in
+ *     double); otherwise FQNM_ERR_ARG.
+ *   - Integer states are int32 for scalar laws and int64 for the Euler
+ *     system, laid out as [nvars][n] (structure of arrays).
+ */
+#ifndef FQNM_H
+#define FQNM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FQNM_OK = 0,
+    FQNM_ERR_ARG = -1,       /* invalid argument (null, size, delta not 2^k) */
+    FQNM_ERR_CFL = -2,       /* Courant number nu = alpha dt/dx > 1 (eq. cfl_number) */
+    FQNM_ERR_RANGE = -3,     /* a state left the range on which the map is verified */
+    FQNM_ERR_OVERFLOW = -4,  /* a state or transfer does not fit its integer type */
+    FQNM_ERR_OOM = -5,       /* device memory or batch memory budget exhausted */
+    FQNM_ERR_CUDA = -6,      /* CUDA runtime error (message in fqnm_last_error) */
+    FQNM_ERR_TIMEOUT = -7,   /* a bounded device or host wait ran out */
+    FQNM_ERR_STATE = -8,     /* call out of order (e.g. step before load) */
+    FQNM_ERR_BUSY = -9       /* batch: no free slot for the request right now */
+} fqnm_status;
+
+typedef enum { FQNM_BC_PERIODIC = 0, FQNM_BC_TRANSMISSIVE = 1 } fqnm_boundary;
+
+/* Rounding of round() in eqs. quantisation and flux_table.  The paper's
+ * prototype rounds half to even (the default); floor is the mean-field
+ * closure n = floor(Np) of eq. mean_field_closure. */
+typedef enum {
+    FQNM_ROUND_HALF_EVEN = 0,
+    FQNM_ROUND_HALF_AWAY = 1,
+    FQNM_ROUND_FLOOR = 2
+} fqnm_rounding;
+
+/* Flux kinds.  Split fluxes f = f+ + f- (eq. flux_splitting):
+ *   LINEAR_UPWIND  f = a u,     f+ = max(a,0) u,  f- = min(a,0) u
+ *   LINEAR_LF      f = a u,     f+- = (f(u) +- alpha u)/2
+ *   BURGERS_LF     f = u^2/2,   f+- = (f(u) +- alpha u)/2
+ *   BURGERS_EO     f = u^2/2,   f+ = max(u,0)^2/2, f- = min(u,0)^2/2
+ *   TABLE          caller-supplied integer maps phi+- (fqnm_create_table):
+ *                  the transfer rule as the primitive object (§2.2, scope of
+ *                  transfer-operator equivalence)
+ *   EULER_ROE      1-D Euler, gamma-law gas, Roe flux quantised per
+ *                  conserved component (§3.3); nvars = 3                    */
+typedef enum {
+    FQNM_FLUX_LINEAR_UPWIND = 0,
+    FQNM_FLUX_LINEAR_LF = 1,
+    FQNM_FLUX_BURGERS_LF = 2,
+    FQNM_FLUX_BURGERS_EO = 3,
+    FQNM_FLUX_TABLE = 8,
+    FQNM_FLUX_EULER_ROE = 16
+} fqnm_flux_kind;
+
+typedef struct {
+    int kind;        /* fqnm_flux_kind */
+    double a;        /* advection speed (linear kinds) */
+    double alpha;    /* LF bound, alpha >= max|f'(u)| (§2, after eq. flux_splitting) */
+    double gamma;    /* ratio of specific heats (EULER_ROE) */
+    int rounding;    /* fqnm_rounding */
+} fqnm_flux;
+
+typedef struct fqnm_solver fqnm_solver;
+
+/* ---- solver lifecycle ---------------------------------------------------- */
+
+/* Create a solver for one problem (§2: grid spacing dx, step dt, quantum
+ * delta).  delta points to nvars values (1 scalar, 3 Euler), each a power of
+ * two.  The Courant number nu = alpha*dt/dx (LF kinds) or |a|*dt/dx (upwind)
+ * must be <= 1 (eq. cfl_number), else FQNM_ERR_CFL.  Touches no GPU: the
+ * transfer rule is built at load time, when the visited range is known.
+ * *out receives a handle to release with fqnm_destroy. */
+fqnm_status fqnm_create(const fqnm_flux* flux, const double* delta, double dx,
+                        double dt, int boundary, fqnm_solver** out);
+
+/* Create a solver whose transfer rule is given directly as integer maps
+ * phi_p[k] = phi+(lo+k), phi_m[k] = phi-(lo+k), k < count (host arrays,
+ * copied).  States must stay in [lo, lo+count-1]; leaving it is
+ * FQNM_ERR_RANGE.  delta only scales the observable. */
+fqnm_status fqnm_create_table(const int32_t* phi_p, const int32_t* phi_m,
+                              int64_t lo, int64_t count, double delta,
+                              int boundary, fqnm_solver** out);
+
+fqnm_status fqnm_destroy(fqnm_solver* s);
+
+/* Use the caller's CUDA stream (a cudaStream_t, e.g. torch's current stream)
+ * for all later work of this handle.  NULL selects the library's own
+ * non-blocking stream. */
+fqnm_status fqnm_set_stream(fqnm_solver* s, void* stream);
+
+/* Options (fqnm_option) that override the automatic execution plan.  Plans
+ * differ in speed only: every plan gives bit-identical states. */
+typedef enum {
+    FQNM_OPT_KERNEL = 0,     /* 0 auto, 1 naive one-step, 2 temporal-blocked */
+    FQNM_OPT_LAYOUT = 1,     /* 0 auto, 1 interleaved, 2 blocked (cells per thread contiguous) */
+    FQNM_OPT_CELLS_PER_THREAD = 2, /* 4, 8 or 16; 0 auto */
+    FQNM_OPT_BLOCK = 3,      /* threads per block, multiple of 32, <= 1024; 0 auto */
+    FQNM_OPT_K = 4,          /* time steps per launch (temporal block depth); 0 auto */
+    FQNM_OPT_MARGIN = 5,     /* quanta added on each side of the loaded range (default 1024) */
+    FQNM_OPT_CLOSED_FORM = 6,/* 1 (default): use a verified integer closed form when one exists */
+    FQNM_OPT_RECOVER = 7,    /* 1 (default): on range escape widen the map and replay */
+    FQNM_OPT_AUTOTUNE = 8,   /* 1: time candidate plans at load and keep the fastest */
+    FQNM_OPT_GRAPH = 9       /* 1 (default): replay long step loops from a CUDA graph */
+} fqnm_option;
+fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
+
+/* ---- states --------------------------------------------------------------- */
+
+/* eq. quantisation on the GPU: q_i = round(u_i/delta) with the given rounding.
+ * u: n doubles; q_out: n int32 (state_bits = 32) or int64 (64).  _device
+ * takes device pointers and runs on `stream` (NULL: legacy default stream);
+ * the host variant stages through device memory.  A value that does not fit
+ * the state type is FQNM_ERR_OVERFLOW. */
+fqnm_status fqnm_quantise(const double* u, size_t n, double delta, int rounding,
+                          int state_bits, void* q_out);
+fqnm_status fqnm_quantise_device(const double* u, size_t n, double delta,
+                                 int rounding, int state_bits, void* q_out,
+                                 void* stream);
+
+/* Load the initial integer state (host or device pointer; int32 [n] for
+ * scalar laws, int64 [3][n] for EULER_ROE).  Builds the transfer rule over
+ * the loaded range (eq. flux_table, on the GPU), verifies any integer closed
+ * form against it, and resets the step counter and boundary-flux totals. */
+fqnm_status fqnm_load_states(fqnm_solver* s, const void* q, size_t n_cells);
+fqnm_status fqnm_load_states_device(fqnm_solver* s, const void* q,
+                                    size_t n_cells);
+
+/* Quantise a double field u ([nvars][n], host or device pointer) on the GPU
+ * with the flux's rounding (eq. quantisation, per-variable delta) and load
+ * it as the initial state, exactly as fqnm_load_states would load the
+ * quantised integers. */
+fqnm_status fqnm_load_field(fqnm_solver* s, const double* u, size_t n_cells,
+                            int on_device);
+
+/* Advance k steps of eq. update_rule (asynchronous). */
+fqnm_status fqnm_step(fqnm_solver* s, uint64_t k);
+
+/* Wait for the handle's stream and report device-side errors. */
+fqnm_status fqnm_sync(fqnm_solver* s);
+
+/* Observable u = delta*q (eq. reconstruction_operator) as double, [nvars][n].
+ * fqnm_observe writes a host buffer and synchronises; _device writes a device
+ * buffer (fp32 != 0: float) asynchronously. */
+fqnm_status fqnm_observe(fqnm_solver* s, double* u_out);
+fqnm_status fqnm_observe_device(fqnm_solver* s, void* u_out, int fp32);
+
+/* Copy the integer state out (host: synchronises; device: asynchronous). */
+fqnm_status fqnm_checkpoint(fqnm_solver* s, void* q_out, uint64_t* step);
+fqnm_status fqnm_checkpoint_device(fqnm_solver* s, void* q_out);
+
+/* Exact integer invariants (Lemma on telescoping conservation, eq.
+ * exact_conservation; Lemma on CFL stability (ii)-(iii)):
+ *   mass[v] = sum_i q^v_i
+ *   tv[v]   = sum_i |q^v_{i+1} - q^v_i| (periodic: includes the wrap face)
+ *   l1[v]   = sum_i |q^v_i - other^v_i| (0 when other is NULL)
+ *   boundary_flux[v] = transfer out of the right end minus into the left end
+ *                      since load; sum q^v(now) = sum q^v(load) - it.
+ * other must have the same shape.  Synchronises. */
+typedef struct {
+    int64_t mass[3];
+    int64_t tv[3];
+    int64_t l1[3];
+    int64_t boundary_flux[3];
+    uint64_t step;
+    int32_t nvars;
+} fqnm_invariants_t;
+fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
+                            fqnm_invariants_t* out);
+
+/* Description of the transfer rule built at load (eq. flux_table). */
+typedef struct {
+    int64_t lo, hi;        /* q range the maps are tabulated and verified on */
+    int32_t evaluator;     /* 1 table gather, 2 integer closed form */
+    int32_t has_plus, has_minus;
+    int32_t monotone;      /* certificate: phi+ nondecreasing, phi- nonincreasing
+                              and q - phi+(q) + phi-(q) nondecreasing on the
+                              range, so the integer update is a monotone scheme */
+    int64_t num, den;      /* closed form phi+(q) = round(q*num/den) when evaluator = 2 */
+    int32_t closed_form_sign; /* +1: closed form is phi+, -1: phi- */
+    int32_t recoveries;    /* range escapes repaired by widening and replay */
+} fqnm_rule_info;
+fqnm_status fqnm_get_rule(fqnm_solver* s, fqnm_rule_info* out);
+
+/* Copy the transfer tables (phi+ and phi- over [lo, hi]) to host arrays of
+ * hi-lo+1 int32 each. */
+fqnm_status fqnm_get_tables(fqnm_solver* s, int32_t* phi_p, int32_t* phi_m);
+
+/* Execution statistics since load (or since the last reset). */
+typedef struct {
+    uint64_t launches;      /* kernels launched by step calls */
+    uint64_t steps;
+    uint64_t cell_updates;  /* n * steps */
+    int32_t kernel;         /* 1 naive, 2 temporal-blocked */
+    int32_t layout, cells_per_thread, block, k;
+    int32_t graph;          /* 1 if step loops are replayed from a CUDA graph */
+} fqnm_stats;
+fqnm_status fqnm_get_stats(fqnm_solver* s, fqnm_stats* out, int reset);
+
+/* ---- floating-point finite-volume baseline -------------------------------- */
+
+/* The classical split finite-volume operator of eq.
+ * classical_operator_definition, u_i <- u_i - dt/dx (F(u_i,u_{i+1}) -
+ * F(u_{i-1},u_i)), F(uL,uR) = f+(uL) + f-(uR), with the same flux as the
+ * integer solver, in float (precision 32) or double (64), one step per
+ * launch, no FMA contraction.  EULER_ROE runs the Roe flux on [3][n]. */
+typedef struct fqnm_fv fqnm_fv;
+fqnm_status fqnm_fv_create(const fqnm_flux* flux, double dx, double dt,
+                           int boundary, int precision, fqnm_fv** out);
+fqnm_status fqnm_fv_destroy(fqnm_fv* f);
+fqnm_status fqnm_fv_set_stream(fqnm_fv* f, void* stream);
+/* u: [nvars][n] doubles (host or device); converted to the precision. */
+fqnm_status fqnm_fv_load(fqnm_fv* f, const double* u, size_t n_cells);
+fqnm_status fqnm_fv_load_device(fqnm_fv* f, const double* u, size_t n_cells);
+fqnm_status fqnm_fv_step(fqnm_fv* f, uint64_t k);
+fqnm_status fqnm_fv_observe(fqnm_fv* f, double* u_out);          /* host, syncs */
+fqnm_status fqnm_fv_observe_device(fqnm_fv* f, double* u_out);   /* device */
+fqnm_status fqnm_fv_launches(fqnm_fv* f, uint64_t* launches);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+
+const char* fqnm_last_error(void);
+/* Number of CUDA kernels this library has launched in this process (kernels
+ * inside a replayed CUDA graph count one each). */
+uint64_t fqnm_kernel_launches(void);
+const char* fqnm_status_string(int status);
+/* Library version as major*10000 + minor*100 + patch. */
+int fqnm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FQNM_H */

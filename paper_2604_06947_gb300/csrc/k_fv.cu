@@ -1,0 +1,168 @@
+// k_fv.cu -- the floating-point finite-volume baseline with the same flux.
+//
+// eq. classical_operator_definition:
+//     u_i <- u_i - lambda * (F_{i+1/2} - F_{i-1/2}),  F(uL,uR) = f+(uL) + f-(uR)
+// in float or double, one step per launch, each operation explicitly rounded
+// (no contraction) in the order
+//     Fr = f+(u_i) + f-(u_{i+1}),  Fl = f+(u_{i-1}) + f-(u_i),
+//     d = Fr - Fl,  u_i - lambda*d
+// with the split fluxes of eq. flux_splitting written as in the rule builder.
+// The Euler variant uses the Roe flux of roe.cuh on [3][n], transmissive ends.
+#include "fqnm_internal.h"
+#include "roe.cuh"
+
+namespace fqnm {
+
+namespace {
+
+template <typename T>
+struct FvParams {
+    int kind;
+    T a, alpha, lambda;
+};
+
+template <typename T>
+__device__ __forceinline__ T fsplit(const FvParams<T>& P, int sign, T u)
+{
+    using A = Ar<T>;
+    switch (P.kind) {
+    case FQNM_FLUX_LINEAR_UPWIND: {
+        const T c = sign > 0 ? (P.a > T(0) ? P.a : T(0)) : (P.a < T(0) ? P.a : T(0));
+        return A::mul(c, u);
+    }
+    case FQNM_FLUX_LINEAR_LF:
+    case FQNM_FLUX_BURGERS_LF: {
+        const T f = P.kind == FQNM_FLUX_LINEAR_LF ? A::mul(P.a, u)
+                                                  : A::mul(T(0.5), A::mul(u, u));
+        const T d = A::mul(P.alpha, u);
+        return A::mul(T(0.5), sign > 0 ? A::add(f, d) : A::sub(f, d));
+    }
+    case FQNM_FLUX_BURGERS_EO: {
+        const T w = sign > 0 ? (u > T(0) ? u : T(0)) : (u < T(0) ? u : T(0));
+        return A::mul(T(0.5), A::mul(w, w));
+    }
+    default:
+        return T(0);
+    }
+}
+
+template <typename T>
+__global__ void k_fv_step(FvParams<T> P, const T* __restrict__ uin,
+                          T* __restrict__ uout, long long n, int periodic)
+{
+    using A = Ar<T>;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long il = i - 1, ir = i + 1;
+        if (periodic) {
+            if (il < 0) il = n - 1;
+            if (ir >= n) ir = 0;
+        } else {
+            if (il < 0) il = 0;
+            if (ir >= n) ir = n - 1;
+        }
+        const T ul = uin[il], uc = uin[i], ur = uin[ir];
+        const T Fr = A::add(fsplit(P, +1, uc), fsplit(P, -1, ur));
+        const T Fl = A::add(fsplit(P, +1, ul), fsplit(P, -1, uc));
+        uout[i] = A::sub(uc, A::mul(P.lambda, A::sub(Fr, Fl)));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void euler_face(const T* __restrict__ u, long long n,
+                                           long long iL, long long iR, T g, T* F)
+{
+    T UL[3], UR[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        UL[k] = u[k * n + iL];
+        UR[k] = u[k * n + iR];
+    }
+    roe_flux<T>(g, UL, UR, F);
+}
+
+template <typename T>
+__global__ void k_euler_fv(T g, T lambda, const T* __restrict__ uin,
+                           T* __restrict__ uout, long long n)
+{
+    using A = Ar<T>;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long c = i < n ? i : n - 1;
+    T Fr[3], Fl[3];
+    euler_face<T>(uin, n, c, c + 1 < n ? c + 1 : n - 1, g, Fr);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
+    if ((threadIdx.x & 31) == 0) euler_face<T>(uin, n, c > 0 ? c - 1 : 0, c, g, Fl);
+    if (i < n) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            uout[k * n + i] = A::sub(uin[k * n + i], A::mul(lambda, A::sub(Fr[k], Fl[k])));
+    }
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A* in, B* out, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (B)in[i];
+}
+
+}  // namespace
+
+cudaError_t launch_fv_step_f64(int kind, double a, double alpha, double lambda,
+                               const double* uin, double* uout, int64_t n,
+                               int periodic, cudaStream_t st)
+{
+    FvParams<double> P{kind, a, alpha, lambda};
+    k_fv_step<double><<<grid_for(n, 256), 256, 0, st>>>(P, uin, uout, n, periodic);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fv_step_f32(int kind, double a, double alpha, double lambda,
+                               const float* uin, float* uout, int64_t n,
+                               int periodic, cudaStream_t st)
+{
+    FvParams<float> P{kind, (float)a, (float)alpha, (float)lambda};
+    k_fv_step<float><<<grid_for(n, 256), 256, 0, st>>>(P, uin, uout, n, periodic);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euler_fv_f64(double gamma, double lambda, const double* uin,
+                                double* uout, int64_t n, cudaStream_t st)
+{
+    const long long grid = (n + 127) / 128;
+    k_euler_fv<double><<<(unsigned)grid, 128, 0, st>>>(gamma, lambda, uin, uout, n);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euler_fv_f32(double gamma, double lambda, const float* uin,
+                                float* uout, int64_t n, cudaStream_t st)
+{
+    const long long grid = (n + 127) / 128;
+    k_euler_fv<float><<<(unsigned)grid, 128, 0, st>>>((float)gamma, (float)lambda,
+                                                      uin, uout, n);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f64_to_f32(const double* in, float* out, int64_t n,
+                                      cudaStream_t st)
+{
+    k_convert<double, float><<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32_to_f64(const float* in, double* out, int64_t n,
+                                      cudaStream_t st)
+{
+    k_convert<float, double><<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+    note_launches();
+    return cudaGetLastError();
+}
+
+}  // namespace fqnm

@@ -1,0 +1,80 @@
+// roe.cuh -- Roe flux of the 1-D Euler equations on the GPU (§3.3).
+//
+// Textbook Roe flux, no entropy fix, gamma-law gas, conserved U = (rho, m, E):
+//   uK = mK/rhoK, pK = (g-1)*(EK - 0.5*(rhoK*(uK*uK))), HK = (EK+pK)/rhoK
+//   sL = sqrt(rhoL), sR = sqrt(rhoR), w = sL + sR
+//   ut = (sL*uL + sR*uR)/w, Ht = (sL*HL + sR*HR)/w
+//   ct = sqrt((g-1)*(Ht - 0.5*(ut*ut)))
+//   jumps d0, d1, d2 of rho, m, E; wave strengths
+//   a2 = (g-1)/(ct*ct) * ((d0*(Ht - ut*ut) + ut*d1) - d2)
+//   a1 = ((d0*(ut+ct) - d1) - ct*a2) / (2*ct),   a3 = d0 - (a1 + a2)
+//   speeds |ut-ct|, |ut|, |ut+ct|; eigenvectors
+//   r1 = (1, ut-ct, Ht-ut*ct), r2 = (1, ut, 0.5*(ut*ut)), r3 = (1, ut+ct, Ht+ut*ct)
+//   F_k = 0.5*(fL_k + fR_k) - 0.5*((l1*a1*r1_k + l2*a2*r2_k) + l3*a3*r3_k)
+// Every operation is an explicitly rounded IEEE operation (no contraction),
+// in this order, so the double version is reproducible bit for bit.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fqnm {
+
+template <typename T> struct Ar;
+
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+    static __device__ __forceinline__ double abs_(double a) { return fabs(a); }
+};
+
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+    static __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
+};
+
+template <typename T>
+__device__ __forceinline__ void roe_flux(T g, const T* UL, const T* UR, T* F)
+{
+    using A = Ar<T>;
+    const T one = T(1), half = T(0.5), gm1 = A::sub(g, one);
+    const T rhoL = UL[0], mL = UL[1], EL = UL[2];
+    const T rhoR = UR[0], mR = UR[1], ER = UR[2];
+    const T uL = A::div(mL, rhoL), uR = A::div(mR, rhoR);
+    const T pL = A::mul(gm1, A::sub(EL, A::mul(half, A::mul(rhoL, A::mul(uL, uL)))));
+    const T pR = A::mul(gm1, A::sub(ER, A::mul(half, A::mul(rhoR, A::mul(uR, uR)))));
+    const T HL = A::div(A::add(EL, pL), rhoL), HR = A::div(A::add(ER, pR), rhoR);
+    const T sL = A::sqrt_(rhoL), sR = A::sqrt_(rhoR), w = A::add(sL, sR);
+    const T ut = A::div(A::add(A::mul(sL, uL), A::mul(sR, uR)), w);
+    const T Ht = A::div(A::add(A::mul(sL, HL), A::mul(sR, HR)), w);
+    const T uu = A::mul(ut, ut);
+    const T ct = A::sqrt_(A::mul(gm1, A::sub(Ht, A::mul(half, uu))));
+    const T d0 = A::sub(rhoR, rhoL), d1 = A::sub(mR, mL), d2 = A::sub(ER, EL);
+    const T a2 = A::mul(A::div(gm1, A::mul(ct, ct)),
+                        A::sub(A::add(A::mul(d0, A::sub(Ht, uu)), A::mul(ut, d1)), d2));
+    const T a1 = A::div(A::sub(A::sub(A::mul(d0, A::add(ut, ct)), d1), A::mul(ct, a2)),
+                        A::mul(T(2), ct));
+    const T a3 = A::sub(d0, A::add(a1, a2));
+    const T l1 = A::abs_(A::sub(ut, ct)), l2 = A::abs_(ut), l3 = A::abs_(A::add(ut, ct));
+    const T uct = A::mul(ut, ct);
+    const T r1[3] = {one, A::sub(ut, ct), A::sub(Ht, uct)};
+    const T r2[3] = {one, ut, A::mul(half, uu)};
+    const T r3[3] = {one, A::add(ut, ct), A::add(Ht, uct)};
+    const T fL[3] = {mL, A::add(A::mul(mL, uL), pL), A::mul(uL, A::add(EL, pL))};
+    const T fR[3] = {mR, A::add(A::mul(mR, uR), pR), A::mul(uR, A::add(ER, pR))};
+    const T la1 = A::mul(l1, a1), la2 = A::mul(l2, a2), la3 = A::mul(l3, a3);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T diss = A::add(A::add(A::mul(la1, r1[k]), A::mul(la2, r2[k])),
+                              A::mul(la3, r3[k]));
+        F[k] = A::sub(A::mul(half, A::add(fL[k], fR[k])), A::mul(half, diss));
+    }
+}
+
+}  // namespace fqnm

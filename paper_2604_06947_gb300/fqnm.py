@@ -1,0 +1,425 @@
+"""Python binding of libfqnm (include/fqnm.h): the same names, argument
+marshalling only.
+
+Every computation runs in the library's CUDA kernels.  There is no fallback:
+if the shared library is missing or cannot be built, load() raises.
+
+Host arrays are numpy arrays; device buffers are anything exposing a device
+pointer (an int, or an object with .data_ptr() such as a torch tensor).
+Every call raises FqnmError on a non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+FQNM_OK = 0
+STATUS = {0: "FQNM_OK", -1: "FQNM_ERR_ARG", -2: "FQNM_ERR_CFL", -3: "FQNM_ERR_RANGE",
+          -4: "FQNM_ERR_OVERFLOW", -5: "FQNM_ERR_OOM", -6: "FQNM_ERR_CUDA",
+          -7: "FQNM_ERR_TIMEOUT", -8: "FQNM_ERR_STATE", -9: "FQNM_ERR_BUSY"}
+FLUX = {"linear_upwind": 0, "linear_lf": 1, "burgers_lf": 2, "burgers_eo": 3,
+        "table": 8, "euler_roe": 16}
+ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
+BOUNDARY = {"periodic": 0, "transmissive": 1}
+OPTION = {"kernel": 0, "layout": 1, "cells_per_thread": 2, "block": 3, "k": 4,
+          "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9}
+
+
+class FqnmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+class fqnm_flux(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_double), ("alpha", C.c_double),
+                ("gamma", C.c_double), ("rounding", C.c_int)]
+
+
+class fqnm_invariants_t(C.Structure):
+    _fields_ = [("mass", C.c_int64 * 3), ("tv", C.c_int64 * 3), ("l1", C.c_int64 * 3),
+                ("boundary_flux", C.c_int64 * 3), ("step", C.c_uint64),
+                ("nvars", C.c_int32)]
+
+
+class fqnm_rule_info(C.Structure):
+    _fields_ = [("lo", C.c_int64), ("hi", C.c_int64), ("evaluator", C.c_int32),
+                ("has_plus", C.c_int32), ("has_minus", C.c_int32),
+                ("monotone", C.c_int32), ("num", C.c_int64), ("den", C.c_int64),
+                ("closed_form_sign", C.c_int32), ("recoveries", C.c_int32)]
+
+
+class fqnm_stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("steps", C.c_uint64),
+                ("cell_updates", C.c_uint64), ("kernel", C.c_int32),
+                ("layout", C.c_int32), ("cells_per_thread", C.c_int32),
+                ("block", C.c_int32), ("k", C.c_int32), ("graph", C.c_int32)]
+
+
+class fqnm_problem_spec(C.Structure):
+    _fields_ = [("flux", fqnm_flux), ("delta", C.c_double), ("dx", C.c_double),
+                ("dt", C.c_double), ("boundary", C.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = C.c_void_p
+_st = C.c_int
+
+# name -> (restype, argtypes)
+PROTOTYPES = {
+    "fqnm_create": (_st, [C.POINTER(fqnm_flux), C.POINTER(C.c_double), C.c_double,
+                          C.c_double, C.c_int, C.POINTER(_vp)]),
+    "fqnm_create_table": (_st, [_vp, _vp, C.c_int64, C.c_int64, C.c_double, C.c_int,
+                                C.POINTER(_vp)]),
+    "fqnm_destroy": (_st, [_vp]),
+    "fqnm_set_stream": (_st, [_vp, _vp]),
+    "fqnm_set_option": (_st, [_vp, C.c_int, C.c_int64]),
+    "fqnm_quantise": (_st, [_vp, C.c_size_t, C.c_double, C.c_int, C.c_int, _vp]),
+    "fqnm_quantise_device": (_st, [_vp, C.c_size_t, C.c_double, C.c_int, C.c_int, _vp, _vp]),
+    "fqnm_load_states": (_st, [_vp, _vp, C.c_size_t]),
+    "fqnm_load_states_device": (_st, [_vp, _vp, C.c_size_t]),
+    "fqnm_load_field": (_st, [_vp, _vp, C.c_size_t, C.c_int]),
+    "fqnm_step": (_st, [_vp, C.c_uint64]),
+    "fqnm_sync": (_st, [_vp]),
+    "fqnm_observe": (_st, [_vp, _vp]),
+    "fqnm_observe_device": (_st, [_vp, _vp, C.c_int]),
+    "fqnm_checkpoint": (_st, [_vp, _vp, C.POINTER(C.c_uint64)]),
+    "fqnm_checkpoint_device": (_st, [_vp, _vp]),
+    "fqnm_invariants": (_st, [_vp, _vp, C.POINTER(fqnm_invariants_t)]),
+    "fqnm_get_rule": (_st, [_vp, C.POINTER(fqnm_rule_info)]),
+    "fqnm_get_tables": (_st, [_vp, _vp, _vp]),
+    "fqnm_get_stats": (_st, [_vp, C.POINTER(fqnm_stats), C.c_int]),
+    "fqnm_fv_create": (_st, [C.POINTER(fqnm_flux), C.c_double, C.c_double, C.c_int,
+                             C.c_int, C.POINTER(_vp)]),
+    "fqnm_fv_destroy": (_st, [_vp]),
+    "fqnm_fv_set_stream": (_st, [_vp, _vp]),
+    "fqnm_fv_load": (_st, [_vp, _vp, C.c_size_t]),
+    "fqnm_fv_load_device": (_st, [_vp, _vp, C.c_size_t]),
+    "fqnm_fv_step": (_st, [_vp, C.c_uint64]),
+    "fqnm_fv_observe": (_st, [_vp, _vp]),
+    "fqnm_fv_observe_device": (_st, [_vp, _vp]),
+    "fqnm_fv_launches": (_st, [_vp, C.POINTER(C.c_uint64)]),
+    "fqnm_last_error": (C.c_char_p, []),
+    "fqnm_status_string": (C.c_char_p, [C.c_int]),
+    "fqnm_version": (C.c_int, []),
+    "fqnm_kernel_launches": (C.c_uint64, []),
+}
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "_build", "libfqnm.so")
+
+
+def load(build: bool = True):
+    """Load libfqnm (building it in-tree first if its sources changed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if build:
+            from . import build as _b
+            path = _b.build()
+        if not os.path.exists(path):
+            raise FqnmError(-6, "libfqnm is not built (%s); run build()" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in PROTOTYPES.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(st: int):
+    if st != FQNM_OK:
+        msg = load().fqnm_last_error()
+        raise FqnmError(st, msg.decode() if msg else "")
+
+
+def _dptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("need a device pointer (int) or an object with data_ptr()")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return getattr(s, "cuda_stream", None) or getattr(s, "ptr", None)
+
+
+def make_flux(kind: str, a: float = 0.0, alpha: float = 0.0, gamma: float = 0.0,
+              rounding: str = "half_even") -> fqnm_flux:
+    return fqnm_flux(FLUX[kind], a, alpha, gamma, ROUNDING[rounding])
+
+
+# ---------------------------------------------------------------------------
+# solver calls (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def fqnm_create(flux: fqnm_flux, delta, dx: float, dt: float,
+                boundary: str = "periodic") -> int:
+    d = np.atleast_1d(np.asarray(delta, dtype=np.float64))
+    out = _vp()
+    _check(load().fqnm_create(C.byref(flux), d.ctypes.data_as(C.POINTER(C.c_double)),
+                              dx, dt, BOUNDARY[boundary], C.byref(out)))
+    return out.value
+
+
+def fqnm_create_table(phi_p, phi_m, lo: int, delta: float,
+                      boundary: str = "periodic") -> int:
+    p = np.ascontiguousarray(phi_p, dtype=np.int32)
+    m = np.ascontiguousarray(phi_m, dtype=np.int32)
+    if p.shape != m.shape:
+        raise ValueError("phi_p and phi_m differ in length")
+    out = _vp()
+    _check(load().fqnm_create_table(p.ctypes.data, m.ctypes.data, lo, p.shape[0], delta,
+                                    BOUNDARY[boundary], C.byref(out)))
+    return out.value
+
+
+def fqnm_destroy(h: int):
+    _check(load().fqnm_destroy(h))
+
+
+def fqnm_set_stream(h: int, stream=None):
+    _check(load().fqnm_set_stream(h, _stream(stream)))
+
+
+def fqnm_set_option(h: int, option: str, value: int):
+    _check(load().fqnm_set_option(h, OPTION[option], int(value)))
+
+
+def fqnm_quantise(u, delta: float, rounding: str = "half_even", state_bits: int = 32):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    q = np.empty(u.shape[0], dtype=np.int32 if state_bits == 32 else np.int64)
+    _check(load().fqnm_quantise(u.ctypes.data, u.shape[0], delta, ROUNDING[rounding],
+                                state_bits, q.ctypes.data))
+    return q
+
+
+def fqnm_quantise_device(u_dev, n: int, delta: float, q_dev, rounding: str = "half_even",
+                         state_bits: int = 32, stream=None):
+    _check(load().fqnm_quantise_device(_dptr(u_dev), n, delta, ROUNDING[rounding],
+                                       state_bits, _dptr(q_dev), _stream(stream)))
+
+
+def fqnm_load_states(h: int, q, nvars: int = 1):
+    q = np.ascontiguousarray(q, dtype=np.int32 if nvars == 1 else np.int64)
+    n = q.shape[-1] if q.ndim > 1 else q.shape[0]
+    if nvars == 3 and q.size != 3 * n:
+        raise ValueError("Euler states must be [3][n]")
+    _check(load().fqnm_load_states(h, q.ctypes.data, n))
+
+
+def fqnm_load_states_device(h: int, q_dev, n_cells: int):
+    _check(load().fqnm_load_states_device(h, _dptr(q_dev), n_cells))
+
+
+def fqnm_load_field(h: int, u, n_cells: Optional[int] = None, on_device: bool = False):
+    """u: numpy [nvars][n] doubles (host) or a device pointer with n_cells."""
+    if on_device:
+        _check(load().fqnm_load_field(h, _dptr(u), n_cells, 1))
+        return
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    _check(load().fqnm_load_field(h, u.ctypes.data, u.shape[-1], 0))
+
+
+def fqnm_step(h: int, k: int):
+    _check(load().fqnm_step(h, k))
+
+
+def fqnm_sync(h: int):
+    _check(load().fqnm_sync(h))
+
+
+def fqnm_observe(h: int, n: int, nvars: int = 1) -> np.ndarray:
+    u = np.empty(n * nvars, dtype=np.float64)
+    _check(load().fqnm_observe(h, u.ctypes.data))
+    return u.reshape(nvars, n) if nvars > 1 else u
+
+
+def fqnm_observe_device(h: int, u_dev, fp32: bool = False):
+    _check(load().fqnm_observe_device(h, _dptr(u_dev), 1 if fp32 else 0))
+
+
+def fqnm_checkpoint(h: int, n: int, nvars: int = 1):
+    q = np.empty(n * nvars, dtype=np.int32 if nvars == 1 else np.int64)
+    step = C.c_uint64(0)
+    _check(load().fqnm_checkpoint(h, q.ctypes.data, C.byref(step)))
+    return (q.reshape(nvars, n) if nvars > 1 else q), step.value
+
+
+def fqnm_checkpoint_device(h: int, q_dev):
+    _check(load().fqnm_checkpoint_device(h, _dptr(q_dev)))
+
+
+def fqnm_invariants(h: int, other: Optional[int] = None) -> dict:
+    out = fqnm_invariants_t()
+    _check(load().fqnm_invariants(h, other or None, C.byref(out)))
+    nv = out.nvars
+    return {"mass": list(out.mass)[:nv], "tv": list(out.tv)[:nv], "l1": list(out.l1)[:nv],
+            "boundary_flux": list(out.boundary_flux)[:nv], "step": out.step}
+
+
+def fqnm_get_rule(h: int) -> dict:
+    out = fqnm_rule_info()
+    _check(load().fqnm_get_rule(h, C.byref(out)))
+    return {f: getattr(out, f) for f, _ in fqnm_rule_info._fields_}
+
+
+def fqnm_get_tables(h: int):
+    r = fqnm_get_rule(h)
+    cnt = r["hi"] - r["lo"] + 1
+    p = np.empty(cnt, dtype=np.int32)
+    m = np.empty(cnt, dtype=np.int32)
+    _check(load().fqnm_get_tables(h, p.ctypes.data, m.ctypes.data))
+    return r["lo"], p, m
+
+
+def fqnm_get_stats(h: int, reset: bool = False) -> dict:
+    out = fqnm_stats()
+    _check(load().fqnm_get_stats(h, C.byref(out), 1 if reset else 0))
+    return {f: getattr(out, f) for f, _ in fqnm_stats._fields_}
+
+
+# ---------------------------------------------------------------------------
+# finite-volume baseline
+# ---------------------------------------------------------------------------
+
+def fqnm_fv_create(flux: fqnm_flux, dx: float, dt: float, boundary: str = "periodic",
+                   precision: int = 64) -> int:
+    out = _vp()
+    _check(load().fqnm_fv_create(C.byref(flux), dx, dt, BOUNDARY[boundary], precision,
+                                 C.byref(out)))
+    return out.value
+
+
+def fqnm_fv_destroy(h: int):
+    _check(load().fqnm_fv_destroy(h))
+
+
+def fqnm_fv_set_stream(h: int, stream=None):
+    _check(load().fqnm_fv_set_stream(h, _stream(stream)))
+
+
+def fqnm_fv_load(h: int, u):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = u.shape[-1]
+    _check(load().fqnm_fv_load(h, u.ctypes.data, n))
+
+
+def fqnm_fv_load_device(h: int, u_dev, n_cells: int):
+    _check(load().fqnm_fv_load_device(h, _dptr(u_dev), n_cells))
+
+
+def fqnm_fv_step(h: int, k: int):
+    _check(load().fqnm_fv_step(h, k))
+
+
+def fqnm_fv_observe(h: int, n: int, nvars: int = 1) -> np.ndarray:
+    u = np.empty(n * nvars, dtype=np.float64)
+    _check(load().fqnm_fv_observe(h, u.ctypes.data))
+    return u.reshape(nvars, n) if nvars > 1 else u
+
+
+def fqnm_fv_observe_device(h: int, u_dev):
+    _check(load().fqnm_fv_observe_device(h, _dptr(u_dev)))
+
+
+def fqnm_fv_launches(h: int) -> int:
+    v = C.c_uint64(0)
+    _check(load().fqnm_fv_launches(h, C.byref(v)))
+    return v.value
+
+
+def fqnm_last_error() -> str:
+    m = load().fqnm_last_error()
+    return m.decode() if m else ""
+
+
+def fqnm_version() -> int:
+    return load().fqnm_version()
+
+
+def fqnm_kernel_launches() -> int:
+    return load().fqnm_kernel_launches()
+
+
+# ---------------------------------------------------------------------------
+# small convenience wrapper (still marshalling only)
+# ---------------------------------------------------------------------------
+
+class Solver:
+    """Owns one fqnm_solver handle; methods call the functions above."""
+
+    def __init__(self, flux: fqnm_flux, delta, dx: float, dt: float,
+                 boundary: str = "periodic", **options):
+        self.nvars = 3 if flux.kind == FLUX["euler_roe"] else 1
+        self.h = fqnm_create(flux, delta, dx, dt, boundary)
+        self.n = 0
+        for k, v in options.items():
+            fqnm_set_option(self.h, k, v)
+
+    @classmethod
+    def for_problem(cls, p, rounding: str = "half_even", **options):
+        """Solver for an inputs.ScalarProblem."""
+        flux = make_flux(p.flux, a=p.a, alpha=p.alpha, rounding=rounding)
+        return cls(flux, p.delta, p.dx, p.dt, p.boundary, **options)
+
+    def load(self, q):
+        q = np.asarray(q)
+        self.n = q.shape[-1]
+        fqnm_load_states(self.h, q, self.nvars)
+        return self
+
+    def load_device(self, q_dev, n):
+        self.n = n
+        fqnm_load_states_device(self.h, q_dev, n)
+        return self
+
+    def step(self, k: int):
+        fqnm_step(self.h, k)
+        return self
+
+    def state(self):
+        return fqnm_checkpoint(self.h, self.n, self.nvars)[0]
+
+    def observe(self):
+        return fqnm_observe(self.h, self.n, self.nvars)
+
+    def invariants(self, other: Optional["Solver"] = None):
+        return fqnm_invariants(self.h, other.h if other else None)
+
+    def rule(self):
+        return fqnm_get_rule(self.h)
+
+    def stats(self, reset=False):
+        return fqnm_get_stats(self.h, reset)
+
+    def close(self):
+        if self.h:
+            fqnm_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,326 @@
+"""Parity of the CUDA scalar path with the oracle: bit-exact integer states.
+
+All states are compared element by element with the oracle on the same
+seeded inputs; at the full 2^24-cell size the oracle computes sampled cells
+one by one from their dependency cones.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_06947_gb300 import fqnm as F
+from paper_2604_06947_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_kw(p):
+    return dict(kind=p.flux, delta=p.delta, dx=p.dx, dt=p.dt, a=p.a, alpha=p.alpha)
+
+
+def gpu_q0(p, rounding="half_even"):
+    return F.fqnm_quantise(p.u0, p.delta, rounding)
+
+
+def run_and_compare(orc, p, q0, steps, every, boundary="periodic", **opts):
+    """Step GPU and oracle side by side; compare at every checkpoint."""
+    s = F.Solver.for_problem(p, **opts)
+    if boundary != "periodic":
+        s.close()
+        s = F.Solver(F.make_flux(p.flux, a=p.a, alpha=p.alpha), p.delta, p.dx, p.dt,
+                     boundary, **opts)
+    s.load(q0)
+    q = q0.astype(np.int64)
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        s.step(k)
+        q = orc.step(q, p.flux, p.delta, p.dx, p.dt, k, a=p.a, alpha=p.alpha,
+                     boundary=boundary)
+        done += k
+        got = s.state()
+        assert np.array_equal(got.astype(np.int64), q), \
+            "mismatch after %d steps at %s" % (done, np.flatnonzero(got != q)[:8])
+    stats = s.stats()
+    s.close()
+    return q, stats
+
+
+# ---------------------------------------------------------------------------
+# quantisation and the transfer rule
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rounding", ["half_even", "half_away", "floor"])
+def test_quantise_matches_oracle(orc, rounding):
+    p = I.linear_advection_problem(n=4096)
+    u = np.concatenate([p.u0, (np.arange(-50, 50) + 0.5) * p.delta])   # exact ties
+    got = F.fqnm_quantise(u, p.delta, rounding)
+    assert np.array_equal(got.astype(np.int64), orc.quantise(u, p.delta, rounding))
+    got64 = F.fqnm_quantise(u * 2 ** 20, p.delta, rounding, state_bits=64)
+    assert np.array_equal(got64, orc.quantise(u * 2 ** 20, p.delta, rounding))
+
+
+def test_quantise_overflow_is_a_status(fq):
+    with pytest.raises(F.FqnmError) as e:
+        F.fqnm_quantise(np.array([1.0, 3e9]), 1.0)
+    assert e.value.status == -4
+
+
+TABLE_CASES = [
+    ("linear_advection", lambda: I.linear_advection_problem(), "half_even"),
+    ("burgers", lambda: I.burgers_problem(n=1 << 14), "half_even"),
+    ("burgers_floor", lambda: I.burgers_problem(n=1 << 14), "floor"),
+    ("burgers_away", lambda: I.burgers_problem(n=1 << 14), "half_away"),
+    ("high_frequency", lambda: I.high_frequency_problem(n=1 << 14, steps=10), "half_even"),
+]
+
+
+@pytest.mark.parametrize("name,make,rounding", TABLE_CASES, ids=[c[0] for c in TABLE_CASES])
+def test_tables_match_oracle(orc, name, make, rounding):
+    p = make()
+    s = F.Solver.for_problem(p, rounding=rounding)
+    s.load(gpu_q0(p))
+    lo, tp, tm = F.fqnm_get_tables(s.h)
+    op, om = orc.split_table(p.flux, p.delta, p.dx, p.dt, lo, tp.shape[0], a=p.a,
+                             alpha=p.alpha, rounding=rounding)
+    assert np.array_equal(tp.astype(np.int64), op)
+    assert np.array_equal(tm.astype(np.int64), om)
+    s.close()
+
+
+def test_closed_forms_found_and_verified(orc):
+    cases = [(I.linear_advection_problem(), (1, 2)),
+             (I.high_frequency_problem(n=1 << 14, steps=10), (9, 10)),
+             (I.burgers_problem(n=1 << 12), None)]
+    for p, nd in cases:
+        s = F.Solver.for_problem(p)
+        s.load(gpu_q0(p))
+        r = s.rule()
+        if nd is None:
+            assert r["evaluator"] == 1 and r["has_minus"]
+        else:
+            assert r["evaluator"] == 2 and (r["num"], r["den"]) == nd
+        s.close()
+
+
+def test_monotonicity_certificate(orc):
+    s = F.Solver.for_problem(I.high_frequency_problem(n=1 << 12, steps=10))
+    s.load(gpu_q0(I.high_frequency_problem(n=1 << 12, steps=10)))
+    assert s.rule()["monotone"] == 1
+    s.close()
+    p = I.burgers_problem(n=1 << 12)
+    s = F.Solver.for_problem(p)
+    s.load(gpu_q0(p))
+    assert s.rule()["monotone"] == 0          # split-rounded LF Burgers (measured)
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# parity of the step
+# ---------------------------------------------------------------------------
+
+def test_linear_advection_1k_full(orc):
+    """Square wave + sine, N = 1024, 2000 steps, checked every 100 steps."""
+    p = I.linear_advection_problem()
+    q, _ = run_and_compare(orc, p, gpu_q0(p), p.steps, 100)
+    assert q.sum() == gpu_q0(p).astype(np.int64).sum()
+
+
+PLANS = [dict(kernel=1)] + [
+    dict(kernel=2, layout=L, cells_per_thread=v, block=b, k=k)
+    for L in (1, 2) for v in (4, 8, 16) for b in (64, 256) for k in (1, 7, 32)
+] + [dict(kernel=2, layout=1, cells_per_thread=8, block=512, k=64),
+     dict(kernel=2, layout=2, cells_per_thread=16, block=512, k=64)]
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=lambda d: "-".join("%s%s" % kv for kv in d.items()))
+def test_every_plan_bit_exact(orc, plan):
+    """Every execution plan the tuner can pick, on sizes with ragged tails."""
+    for n in (1, 3, 33, 1000, 5003):
+        p = I.burgers_problem(n=n, steps=0)
+        q0 = gpu_q0(p)
+        run_and_compare(orc, p, q0, 75, 75, graph=0, **plan)
+    p = I.high_frequency_problem(n=9001, steps=0)
+    run_and_compare(orc, p, gpu_q0(p), 75, 75, graph=0, **plan)
+
+
+def test_graph_replay_bit_exact(orc):
+    p = I.burgers_problem(n=70_001, steps=0)
+    _, st = run_and_compare(orc, p, gpu_q0(p), 8 * 64 * 2 + 13, 8 * 64 * 2 + 13,
+                            k=8, graph=1)
+    assert st["graph"] == 1
+
+
+def test_burgers_1m_full(orc):
+    """N = 2^20 Burgers, 10^4 steps, every integer state checked every 100
+    steps against the oracle (the bench's workload, the tuned plan)."""
+    p = I.burgers_problem()
+    q, st = run_and_compare(orc, p, gpu_q0(p), p.steps, 100, autotune=1)
+    assert st["kernel"] == 2
+
+
+def test_high_frequency_reduced_full(orc):
+    p = I.high_frequency_problem(n=1 << 16)
+    run_and_compare(orc, p, gpu_q0(p), p.steps, 100)
+
+
+def test_high_frequency_16m_sampled(orc):
+    """Full size (2^24 cells, 2000 steps, tuned plan): 24 sampled cells from
+    the oracle's dependency cones, plus exact mass and the max principle."""
+    p = I.high_frequency_problem()
+    q0 = gpu_q0(p)
+    s = F.Solver.for_problem(p, autotune=1)
+    s.load(q0)
+    s.step(p.steps)
+    q = s.state()
+    rng = np.random.default_rng(11)
+    idx = np.concatenate([[0, 1, p.n - 1, p.n // 2], rng.integers(0, p.n, 20)])
+    q0_64 = q0.astype(np.int64)
+    for i in idx:
+        want = orc.cone(q0_64, int(i), p.steps, p.flux, p.delta, p.dx, p.dt, a=p.a)
+        assert q[i] == want, (i, q[i], want)
+    inv = s.invariants()
+    assert inv["mass"][0] == int(q0_64.sum())
+    assert q.min() >= q0.min() and q.max() <= q0.max()        # certificate holds
+    s.close()
+
+
+def test_transmissive_ends_and_boundary_flux(orc):
+    p = I.burgers_problem(n=3001, steps=0)
+    q0 = gpu_q0(p)
+    q, _ = run_and_compare(orc, p, q0, 400, 100, boundary="transmissive")
+    s = F.Solver(F.make_flux(p.flux, alpha=p.alpha), p.delta, p.dx, p.dt, "transmissive")
+    s.load(q0).step(400)
+    inv = s.invariants()
+    _, bf = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 400, alpha=p.alpha,
+                     boundary="transmissive", return_bflux=True)
+    assert inv["boundary_flux"][0] == bf
+    assert inv["mass"][0] == int(q0.astype(np.int64).sum()) - bf
+    s.close()
+
+
+def test_other_fluxes_and_roundings(orc):
+    for kind, a, alpha, rounding in (("linear_lf", -0.6, 0.9, "half_even"),
+                                     ("linear_lf", 0.6, 0.6, "floor"),
+                                     ("burgers_eo", 0.0, 1.3, "half_away"),
+                                     ("linear_upwind", -1.0, 0.0, "half_even")):
+        p = I.burgers_problem(n=2047, steps=0)
+        p.flux, p.a, p.alpha = kind, a, alpha
+        p.dt = 0.45 * p.dx / max(abs(a), alpha, 1e-9)
+        q0 = gpu_q0(p)
+        s = F.Solver(F.make_flux(kind, a=a, alpha=alpha, rounding=rounding), p.delta,
+                     p.dx, p.dt)
+        s.load(q0).step(333)
+        q = orc.step(q0, kind, p.delta, p.dx, p.dt, 333, a=a, alpha=alpha,
+                     rounding=rounding)
+        assert np.array_equal(s.state().astype(np.int64), q), (kind, rounding)
+        s.close()
+
+
+# ---------------------------------------------------------------------------
+# invariants, observable, checkpoints, device interop
+# ---------------------------------------------------------------------------
+
+def test_invariants_match_oracle(orc):
+    p = I.burgers_problem(n=50_000, steps=0)
+    q0 = gpu_q0(p)
+    a = F.Solver.for_problem(p).load(q0).step(321)
+    b = F.Solver.for_problem(p).load(q0).step(17)
+    inv = a.invariants(b)
+    qa = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 321, alpha=p.alpha)
+    qb = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 17, alpha=p.alpha)
+    mass, tv, l1 = orc.invariants(qa, qb)
+    assert (inv["mass"][0], inv["tv"][0], inv["l1"][0]) == (mass, tv, l1)
+    assert inv["step"] == 321
+    a.close(); b.close()
+
+
+def test_observe_is_delta_times_q(orc):
+    p = I.burgers_problem(n=12_345, steps=0)
+    s = F.Solver.for_problem(p).load(gpu_q0(p)).step(50)
+    q = s.state()
+    u = s.observe()
+    assert np.array_equal(u, p.delta * q.astype(np.float64))
+    import torch
+    d32 = torch.empty(p.n, dtype=torch.float32, device="cuda")
+    F.fqnm_observe_device(s.h, d32, fp32=True)
+    F.fqnm_sync(s.h)
+    assert np.array_equal(d32.cpu().numpy(), (p.delta * q.astype(np.float64)).astype(np.float32))
+    s.close()
+
+
+def test_checkpoint_resume_is_bit_identical(orc):
+    p = I.burgers_problem(n=40_000, steps=0)
+    q0 = gpu_q0(p)
+    a = F.Solver.for_problem(p).load(q0).step(500)
+    b = F.Solver.for_problem(p).load(q0).step(300)
+    mid, step = F.fqnm_checkpoint(b.h, p.n)
+    assert step == 300
+    c = F.Solver.for_problem(p).load(mid).step(200)
+    assert np.array_equal(a.state(), c.state())
+    for s in (a, b, c):
+        s.close()
+
+
+def test_torch_device_buffers_and_stream(orc):
+    import torch
+    p = I.burgers_problem(n=100_000, steps=0)
+    u = torch.from_numpy(p.u0).cuda()
+    q = torch.empty(p.n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    F.fqnm_quantise_device(u, p.n, p.delta, q, stream=stream)
+    s = F.Solver.for_problem(p)
+    F.fqnm_set_stream(s.h, stream)
+    s.load_device(q, p.n).step(250)
+    out = torch.empty(p.n, dtype=torch.int32, device="cuda")
+    F.fqnm_checkpoint_device(s.h, out)
+    stream.synchronize()
+    want = orc.step(orc.quantise(p.u0, p.delta), p.flux, p.delta, p.dx, p.dt, 250,
+                    alpha=p.alpha)
+    assert np.array_equal(out.cpu().numpy().astype(np.int64), want)
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# range escape: detection and exact recovery (no fault, a status)
+# ---------------------------------------------------------------------------
+
+def test_range_escape_is_recovered_exactly(orc):
+    """Split-rounded LF Burgers can overshoot the initial range by a few quanta
+    (the rounded maps are not monotone everywhere).  With no margin the state
+    leaves the table; the library widens the map and replays from its last
+    checkpoint, and the result is still bit-exact."""
+    p = I.burgers_problem(n=4096, steps=0)
+    q0 = gpu_q0(p)
+    s = F.Solver.for_problem(p, margin=0)
+    s.load(q0).step(2000)
+    got = s.state()
+    want = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 2000, alpha=p.alpha)
+    assert np.array_equal(got.astype(np.int64), want)
+    assert want.max() > q0.max() or want.min() < q0.min()
+    assert s.rule()["recoveries"] >= 1
+    s.close()
+
+
+def test_range_escape_without_recovery_is_a_status(orc):
+    p = I.burgers_problem(n=4096, steps=0)
+    s = F.Solver.for_problem(p, margin=0, recover=0)
+    s.load(gpu_q0(p)).step(2000)
+    with pytest.raises(F.FqnmError) as e:
+        F.fqnm_sync(s.h)
+    assert e.value.status == -3
+    s.close()
+
+
+def test_user_supplied_transfer_table(orc):
+    """The transfer rule as the primitive object: caller-supplied maps."""
+    p = I.burgers_problem(n=3000, steps=0)
+    q0 = gpu_q0(p)
+    lo, hi = int(q0.min()) - 500, int(q0.max()) + 500
+    tp, tm = orc.split_table("burgers_eo", p.delta, p.dx, p.dt, lo, hi - lo + 1)
+    h = F.fqnm_create_table(tp.astype(np.int32), tm.astype(np.int32), lo, p.delta)
+    F.fqnm_load_states(h, q0)
+    F.fqnm_step(h, 200)
+    got, _ = F.fqnm_checkpoint(h, p.n)
+    want = orc.step(q0, "burgers_eo", p.delta, p.dx, p.dt, 200)
+    assert np.array_equal(got.astype(np.int64), want)
+    F.fqnm_destroy(h)
