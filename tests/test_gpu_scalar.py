@@ -284,25 +284,36 @@ def test_torch_device_buffers_and_stream(orc):
 # range escape: detection and exact recovery (no fault, a status)
 # ---------------------------------------------------------------------------
 
+def escaping_problem():
+    p = I.burgers_problem(n=4096, steps=0, seed=6)
+    p.alpha = 1.0
+    p.dt = 0.4 * p.dx / p.alpha
+    return p
+
+
 def test_range_escape_is_recovered_exactly(orc):
-    """Split-rounded LF Burgers can overshoot the initial range by a few quanta
-    (the rounded maps are not monotone everywhere).  With no margin the state
-    leaves the table; the library widens the map and replays from its last
-    checkpoint, and the result is still bit-exact."""
-    p = I.burgers_problem(n=4096, steps=0)
+    """With alpha = 1.0 below max|u| = 1.3 the LF split is not monotone and the
+    states overshoot the initial range (by up to 70 quanta for this seed).
+    With no margin the state leaves the table; the library widens the map and
+    replays from its last checkpoint, and the result is still bit-exact."""
+    p = escaping_problem()
     q0 = gpu_q0(p)
+    # the oracle trajectory leaves [min q0, max q0] at some step
+    q, escaped = q0.astype(np.int64), False
+    for _ in range(100):
+        q = orc.step(q, p.flux, p.delta, p.dx, p.dt, 20, alpha=p.alpha)
+        escaped |= bool(q.max() > q0.max() or q.min() < q0.min())
+    assert escaped
     s = F.Solver.for_problem(p, margin=0)
     s.load(q0).step(2000)
     got = s.state()
-    want = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 2000, alpha=p.alpha)
-    assert np.array_equal(got.astype(np.int64), want)
-    assert want.max() > q0.max() or want.min() < q0.min()
+    assert np.array_equal(got.astype(np.int64), q)
     assert s.rule()["recoveries"] >= 1
     s.close()
 
 
 def test_range_escape_without_recovery_is_a_status(orc):
-    p = I.burgers_problem(n=4096, steps=0)
+    p = escaping_problem()
     s = F.Solver.for_problem(p, margin=0, recover=0)
     s.load(gpu_q0(p)).step(2000)
     with pytest.raises(F.FqnmError) as e:
