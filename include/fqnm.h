@@ -197,6 +197,31 @@ typedef struct {
 fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
                             fqnm_invariants_t* out);
 
+/* Allocation-free invariants of a caller's int32 state.  The paper has no
+ * counterpart to this call; it exists for callers that cannot let a library
+ * allocate device memory: processes whose free device memory is held by
+ * their own pool (a caching allocator such as PyTorch's keeps freed blocks,
+ * so an outside cudaMalloc can fail while the pool has room), latency-critical
+ * loops (cudaFree waits for the whole device) and services that must not grow
+ * their device footprint after start-up.
+ * Computes, like fqnm_invariants for one variable, out[0] = sum q,
+ * out[1] = total variation (boundary FQNM_BC_PERIODIC includes the wrap face),
+ * out[2] = sum |q - other| (0 when other is NULL).  q and other are device
+ * pointers to n int32 (caller-owned, only read); out is a host int64[3].  Runs
+ * on `stream` (NULL: legacy default stream) and waits for it before returning.
+ * Its scratch is one static device array reserved on each GPU that loads the
+ * library until the process exits; it calls no cudaMalloc or cudaFree.
+ *   - n must be 1 .. FQNM_NOALLOC_MAX_CELLS, else FQNM_ERR_ARG (no launch).
+ *   - The first call on each device looks up the array's address with that
+ *     device current; make it before any stream capture on that device.
+ *   - All calls on a device share the array and it keeps the last call's
+ *     contents (every slot a call reads is overwritten by that call first).
+ *     Calls whose GPU work overlaps race on it: serialise them. */
+#define FQNM_NOALLOC_MAX_CELLS (1LL << 26)
+fqnm_status fqnm_invariants_noalloc(const int32_t* q, const int32_t* other,
+                                    size_t n, int boundary, int64_t* out,
+                                    void* stream);
+
 /* Description of the transfer rule built at load (eq. flux_table). */
 typedef struct {
     int64_t lo, hi;        /* q range the maps are tabulated and verified on */

@@ -93,6 +93,8 @@ PROTOTYPES = {
     "fqnm_checkpoint": (_st, [_vp, _vp, C.POINTER(C.c_uint64)]),
     "fqnm_checkpoint_device": (_st, [_vp, _vp]),
     "fqnm_invariants": (_st, [_vp, _vp, C.POINTER(fqnm_invariants_t)]),
+    "fqnm_invariants_noalloc": (_st, [_vp, _vp, C.c_size_t, C.c_int,
+                                      C.POINTER(C.c_int64), _vp]),
     "fqnm_get_rule": (_st, [_vp, C.POINTER(fqnm_rule_info)]),
     "fqnm_get_tables": (_st, [_vp, _vp, _vp]),
     "fqnm_get_stats": (_st, [_vp, C.POINTER(fqnm_stats), C.c_int]),
@@ -276,6 +278,16 @@ def fqnm_invariants(h: int, other: Optional[int] = None) -> dict:
     nv = out.nvars
     return {"mass": list(out.mass)[:nv], "tv": list(out.tv)[:nv], "l1": list(out.l1)[:nv],
             "boundary_flux": list(out.boundary_flux)[:nv], "step": out.step}
+
+
+def fqnm_invariants_noalloc(q_dev, n: int, other_dev=None, boundary: str = "periodic",
+                            stream=None) -> tuple:
+    """(mass, total variation, l1) of a device int32 state, computed with the
+    library's static scratch array: no device allocation per call."""
+    out = (C.c_int64 * 3)()
+    _check(load().fqnm_invariants_noalloc(_dptr(q_dev), _dptr(other_dev) or None, n,
+                                          BOUNDARY[boundary], out, _stream(stream)))
+    return out[0], out[1], out[2]
 
 
 def fqnm_get_rule(h: int) -> dict:
