@@ -184,6 +184,7 @@ def run_gpu(args):
     launches0 = F.fqnm_kernel_launches()
     step_ms, region_ms = [], []
     step_launches = 0
+    torch.cuda.nvtx.range_push("bench_timed")      # ncu --nvtx-include bench_timed/
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
             flush.zero_()                                   # evict L2 between steps
@@ -198,6 +199,7 @@ def run_gpu(args):
             step_launches += F.fqnm_get_stats(s.h)["launches"]   # reset by each load
             assert inv["mass"][0] == mass0, "mass not conserved"
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = F.fqnm_kernel_launches() - launches0
     stats = F.fqnm_get_stats(s.h)
     clk = clocks.stop()
@@ -218,7 +220,7 @@ def run_gpu(args):
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peak()
     kernel_tag = "k_step_tb:L%d:V%d" % (stats["layout"], stats["cells_per_thread"])
-    traffic = profiled_traffic(kernel_tag, B.source_digest())
+    traffic = profiled_traffic(kernel_tag, B.kernel_digest())
 
     # end to end through the C ABI with host buffers (rank-local)
     u0_host = torch.from_numpy(p.u0).pin_memory()

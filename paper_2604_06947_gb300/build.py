@@ -58,6 +58,15 @@ def source_digest() -> str:
     return _digest(files)
 
 
+STEP_KERNEL_SOURCES = ("k_scalar.cu", "closed_form.cuh", "fqnm_internal.h")
+
+
+def kernel_digest(files=STEP_KERNEL_SOURCES) -> str:
+    """Digest of the sources of one kernel (default: the stepping kernel), so
+    that a profile taken on them can be matched to the current build."""
+    return _digest([os.path.join(CSRC, f) for f in files])[:16]
+
+
 def _compile(cu: str, verbose: bool) -> str:
     src = os.path.join(CSRC, cu)
     obj = os.path.join(BUILD, cu[:-3] + ".o")
