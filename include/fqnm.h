@@ -271,6 +271,59 @@ fqnm_status fqnm_fv_observe(fqnm_fv* f, double* u_out);          /* host, syncs 
 fqnm_status fqnm_fv_observe_device(fqnm_fv* f, double* u_out);   /* device */
 fqnm_status fqnm_fv_launches(fqnm_fv* f, uint64_t* launches);
 
+/* ---- batched serving ------------------------------------------------------ */
+
+/* Continuous batching of many independent periodic scalar problems of uneven
+ * size and step count (each one the method of §2 on its own grid).  Waiting
+ * problems are admitted as slots and device memory (the budget, one arena
+ * allocated at create) free up; every epoch one persistent launch, replayed
+ * from a CUDA graph, advances every active problem by up to K steps of the
+ * temporal-blocked update; finished states are copied to host memory.  Each
+ * result is bit-identical to solving the problem alone with fqnm_step. */
+typedef struct fqnm_batch fqnm_batch;
+typedef struct {
+    fqnm_flux flux;        /* a scalar split flux (not TABLE or EULER_ROE) */
+    double delta, dx, dt;  /* as in fqnm_create; delta a power of two */
+    int boundary;          /* FQNM_BC_PERIODIC */
+} fqnm_problem_spec;
+
+/* mem_budget_bytes: device arena for states and transfer tables (allocated
+ * here); max_slots: problems on the device at once; stream: NULL for the
+ * library's own.  FQNM_ERR_OOM if the arena cannot be allocated. */
+fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
+                              void* stream, fqnm_batch** out);
+fqnm_status fqnm_batch_destroy(fqnm_batch* b);
+/* Execution plan of the batched launch (0 keeps a value): cells per thread
+ * (4, 8, 16), threads per block, steps per epoch K, layout (1 interleaved, 2
+ * blocked).  Only while no problem is active. */
+fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
+                                int k, int layout);
+/* Queue a problem: q0 is a host int32 [n] (copied), `steps` time steps.
+ * arrival_ns (fqnm_clock_ns clock; 0 = now) is when the request arrives: it
+ * is not admitted before, and its latency is measured from it.  Validates
+ * like fqnm_create.  *id receives its ticket (0, 1, 2, ...). */
+fqnm_status fqnm_batch_submit(fqnm_batch* b, const fqnm_problem_spec* spec,
+                              const int32_t* q0, size_t n, uint64_t steps,
+                              uint64_t arrival_ns, int64_t* id);
+/* Run up to max_epochs epochs (admission, one batched launch, retirement),
+ * stopping early when nothing has arrived or is active.  Reports how many
+ * problems are on the device and how many still wait. */
+fqnm_status fqnm_batch_progress(fqnm_batch* b, int max_epochs, int* n_active,
+                                int* n_queued);
+/* If problem `id` is finished: copy its final state to q_out (host int32 [n],
+ * may be NULL), its arrival-to-result latency in ns, set *done = 1 and
+ * release the result (a second poll is FQNM_ERR_STATE).  Else *done = 0. */
+fqnm_status fqnm_batch_poll(fqnm_batch* b, int64_t id, int32_t* q_out,
+                            uint64_t* latency_ns, int* done);
+/* Pop up to max_ids tickets of problems finished since the last call (in
+ * completion order) into ids; *n receives how many. */
+fqnm_status fqnm_batch_completed(fqnm_batch* b, int64_t* ids, int max_ids, int* n);
+/* Batched launches, cell updates and epochs executed so far. */
+fqnm_status fqnm_batch_stats(fqnm_batch* b, uint64_t* launches,
+                             uint64_t* cell_updates, uint64_t* epochs);
+/* The monotonic clock (ns) the batch uses for arrivals and latencies. */
+uint64_t fqnm_clock_ns(void);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 
 const char* fqnm_last_error(void);

@@ -61,7 +61,7 @@ static int bit_length(uint64_t x)
 
 // Build the closed form for phi(q) = R(q*num/den) on [lo, hi]; false if the
 // 32-bit evaluation would not be exact there.
-static bool make_closed_form(int64_t lo, int64_t hi, uint32_t num, uint32_t den,
+bool make_closed_form(int64_t lo, int64_t hi, uint32_t num, uint32_t den,
                              int rounding, ClosedForm* out)
 {
     if (num == 0 || den == 0 || hi < lo) return false;
@@ -88,7 +88,7 @@ static bool make_closed_form(int64_t lo, int64_t hi, uint32_t num, uint32_t den,
 }
 
 // Continued-fraction convergents of c > 0 with denominators <= maxden.
-static std::vector<std::pair<uint32_t, uint32_t>> convergents(double c, uint32_t maxden)
+std::vector<std::pair<uint32_t, uint32_t>> convergents(double c, uint32_t maxden)
 {
     std::vector<std::pair<uint32_t, uint32_t>> out;
     if (!(c > 0.0) || !std::isfinite(c)) return out;

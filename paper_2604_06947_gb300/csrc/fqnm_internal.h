@@ -6,6 +6,8 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <utility>
+#include <vector>
 
 #include "../../include/fqnm.h"
 
@@ -134,6 +136,10 @@ cudaError_t launch_convert_f32_to_f64(const float* in, double* out, int64_t n,
 extern std::atomic<unsigned long long> g_kernel_launches;
 inline void note_launches(unsigned long long k = 1) { g_kernel_launches.fetch_add(k); }
 fqnm_status set_error(fqnm_status st, const char* fmt, ...);
+// closed-form candidates of a linear map (rule builder)
+bool make_closed_form(int64_t lo, int64_t hi, uint32_t num, uint32_t den, int rounding,
+                      ClosedForm* out);
+std::vector<std::pair<uint32_t, uint32_t>> convergents(double c, uint32_t maxden);
 fqnm_status cuda_error(cudaError_t e, const char* where);
 
 inline unsigned grid_for(int64_t n, int block, int max_blocks = 152 * 16)

@@ -138,11 +138,27 @@ k_rule_check(const int2* tab2, long long lo, long long count, ClosedForm cf,
             if (h1 < h0) flags |= CERT_H_NOT_MONOTONE;
         }
     }
+    // one atomic per block and result: reduce over the warp, then the block
     unsigned long long s = block_sum_u64<CHECK_BLOCK>(mism);
-    if (threadIdx.x == 0 && s) atomicAdd(out + 0, s);
-    if (flags) atomicOr(out + 1, flags);
-    if (maxp) atomicMax(out + 2, maxp);
-    if (maxm) atomicMax(out + 3, maxm);
+    __shared__ unsigned shf[CHECK_BLOCK / 32], shp[CHECK_BLOCK / 32], shm[CHECK_BLOCK / 32];
+    const unsigned f = __reduce_or_sync(0xffffffffu, (unsigned)flags);
+    const unsigned mp = __reduce_max_sync(0xffffffffu, (unsigned)maxp);
+    const unsigned mm = __reduce_max_sync(0xffffffffu, (unsigned)maxm);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { shf[w] = f; shp[w] = mp; shm[w] = mm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned bf = 0, bp = 0, bm = 0;
+        for (int i = 0; i < CHECK_BLOCK / 32; ++i) {
+            bf |= shf[i];
+            bp = bp > shp[i] ? bp : shp[i];
+            bm = bm > shm[i] ? bm : shm[i];
+        }
+        if (s) atomicAdd(out + 0, s);
+        if (bf) atomicOr(out + 1, (unsigned long long)bf);
+        if (bp) atomicMax(out + 2, (unsigned long long)bp);
+        if (bm) atomicMax(out + 3, (unsigned long long)bm);
+    }
 }
 
 template <typename T>

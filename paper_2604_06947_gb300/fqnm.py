@@ -108,6 +108,17 @@ PROTOTYPES = {
     "fqnm_fv_observe": (_st, [_vp, _vp]),
     "fqnm_fv_observe_device": (_st, [_vp, _vp]),
     "fqnm_fv_launches": (_st, [_vp, C.POINTER(C.c_uint64)]),
+    "fqnm_batch_create": (_st, [C.c_size_t, C.c_int, _vp, C.POINTER(_vp)]),
+    "fqnm_batch_destroy": (_st, [_vp]),
+    "fqnm_batch_set_plan": (_st, [_vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "fqnm_batch_submit": (_st, [_vp, C.POINTER(fqnm_problem_spec), _vp, C.c_size_t,
+                                C.c_uint64, C.c_uint64, C.POINTER(C.c_int64)]),
+    "fqnm_batch_progress": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fqnm_batch_poll": (_st, [_vp, C.c_int64, _vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
+    "fqnm_batch_completed": (_st, [_vp, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int)]),
+    "fqnm_batch_stats": (_st, [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                               C.POINTER(C.c_uint64)]),
+    "fqnm_clock_ns": (C.c_uint64, []),
     "fqnm_last_error": (C.c_char_p, []),
     "fqnm_status_string": (C.c_char_p, [C.c_int]),
     "fqnm_version": (C.c_int, []),
@@ -359,6 +370,71 @@ def fqnm_fv_launches(h: int) -> int:
     v = C.c_uint64(0)
     _check(load().fqnm_fv_launches(h, C.byref(v)))
     return v.value
+
+
+# ---------------------------------------------------------------------------
+# batched serving
+# ---------------------------------------------------------------------------
+
+def make_spec(p) -> fqnm_problem_spec:
+    """Problem spec for an inputs.ScalarProblem."""
+    return fqnm_problem_spec(make_flux(p.flux, a=p.a, alpha=p.alpha), p.delta, p.dx, p.dt,
+                             BOUNDARY[p.boundary])
+
+
+def fqnm_batch_create(mem_budget_bytes: int, max_slots: int, stream=None) -> int:
+    out = _vp()
+    _check(load().fqnm_batch_create(mem_budget_bytes, max_slots, _stream(stream), C.byref(out)))
+    return out.value
+
+
+def fqnm_batch_destroy(b: int):
+    _check(load().fqnm_batch_destroy(b))
+
+
+def fqnm_batch_set_plan(b: int, cells_per_thread: int = 0, block: int = 0, k: int = 0,
+                        layout: int = 0):
+    _check(load().fqnm_batch_set_plan(b, cells_per_thread, block, k, layout))
+
+
+def fqnm_batch_submit(b: int, spec: fqnm_problem_spec, q0, steps: int,
+                      arrival_ns: int = 0) -> int:
+    q = np.ascontiguousarray(q0, dtype=np.int32)
+    rid = C.c_int64(0)
+    _check(load().fqnm_batch_submit(b, C.byref(spec), q.ctypes.data, q.shape[0], steps,
+                                    arrival_ns, C.byref(rid)))
+    return rid.value
+
+
+def fqnm_batch_progress(b: int, max_epochs: int = 1):
+    a, q = C.c_int(0), C.c_int(0)
+    _check(load().fqnm_batch_progress(b, max_epochs, C.byref(a), C.byref(q)))
+    return a.value, q.value
+
+
+def fqnm_batch_poll(b: int, rid: int, n: int):
+    """(state or None, latency_ns) -- the state is released on success."""
+    q = np.empty(n, dtype=np.int32)
+    lat, done = C.c_uint64(0), C.c_int(0)
+    _check(load().fqnm_batch_poll(b, rid, q.ctypes.data, C.byref(lat), C.byref(done)))
+    return (q, lat.value) if done.value else (None, 0)
+
+
+def fqnm_batch_completed(b: int, max_ids: int = 4096):
+    ids = (C.c_int64 * max_ids)()
+    n = C.c_int(0)
+    _check(load().fqnm_batch_completed(b, ids, max_ids, C.byref(n)))
+    return list(ids[:n.value])
+
+
+def fqnm_batch_stats(b: int) -> dict:
+    l, c, e = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0)
+    _check(load().fqnm_batch_stats(b, C.byref(l), C.byref(c), C.byref(e)))
+    return {"launches": l.value, "cell_updates": c.value, "epochs": e.value}
+
+
+def fqnm_clock_ns() -> int:
+    return load().fqnm_clock_ns()
 
 
 def fqnm_last_error() -> str:

@@ -1,0 +1,102 @@
+"""Batched serving: every result bit-exact, the same alone and in the mix,
+admission bounded by the memory budget and the slots."""
+import numpy as np
+import pytest
+
+from paper_2604_06947_gb300 import fqnm as F
+from paper_2604_06947_gb300 import inputs as I
+from paper_2604_06947_gb300 import serve as S
+
+pytestmark = pytest.mark.gpu
+
+
+def small_stream(n_requests=48, seed=7, n_max=1 << 14, steps_max=800):
+    return I.serving_stream(n_requests=n_requests, rate_hz=20_000.0, n_min=256,
+                            n_max=n_max, steps_min=50, steps_max=steps_max, seed=seed)
+
+
+def test_batched_results_equal_single_and_oracle(orc):
+    reqs = small_stream()
+    q0s = S.prepare(reqs)
+    # 6 slots and a 3 MiB budget: requests wait for slots and memory
+    bat = S.serve_batched(reqs, q0s, budget_bytes=3 << 20, max_slots=6)
+    one = S.serve_one_by_one(reqs, q0s)
+    for i in range(len(reqs)):
+        assert np.array_equal(bat["results"][i], one["results"][i]), i
+    for i in (0, 1, 2, len(reqs) - 1):
+        p = reqs[i].problem
+        want = orc.step(q0s[i], p.flux, p.delta, p.dx, p.dt, p.steps, a=p.a, alpha=p.alpha)
+        assert np.array_equal(bat["results"][i].astype(np.int64), want), i
+    assert bat["epochs"] >= max(r.problem.steps for r in reqs) // 32
+    assert bat["p99_ms"] >= bat["p50_ms"] > 0
+
+
+def test_same_alone_and_in_the_mix():
+    reqs = small_stream(seed=9)
+    q0s = S.prepare(reqs)
+    mix = S.serve_batched(reqs, q0s, budget_bytes=64 << 20, max_slots=64)
+    for i in (3, 17, 40):
+        alone = S.serve_batched([reqs[i]], [q0s[i]], budget_bytes=64 << 20, max_slots=1)
+        assert np.array_equal(alone["results"][0], mix["results"][i])
+
+
+@pytest.mark.parametrize("plan", [dict(cells_per_thread=4, block=256, k=16, layout=2),
+                                  dict(cells_per_thread=16, block=128, k=64, layout=2),
+                                  dict(cells_per_thread=8, block=256, k=32, layout=1)])
+def test_every_batch_plan_gives_the_same_results(plan):
+    reqs = small_stream(n_requests=24, seed=11)
+    q0s = S.prepare(reqs)
+    ref = S.serve_one_by_one(reqs, q0s)
+    bat = S.serve_batched(reqs, q0s, budget_bytes=64 << 20, max_slots=16, plan=plan)
+    for i in range(len(reqs)):
+        assert np.array_equal(bat["results"][i], ref["results"][i]), (plan, i)
+
+
+def test_large_problems_in_the_mix(orc):
+    """Problems up to 2^20 cells next to small ones (sampled cells checked
+    against the oracle's dependency cones)."""
+    reqs = I.serving_stream(n_requests=12, rate_hz=5000.0, n_min=256, n_max=1 << 20,
+                            steps_min=100, steps_max=1500, seed=13)
+    q0s = S.prepare(reqs)
+    bat = S.serve_batched(reqs, q0s, budget_bytes=1 << 30, max_slots=32)
+    big = max(range(len(reqs)), key=lambda i: reqs[i].problem.n)
+    p = reqs[big].problem
+    rng = np.random.default_rng(5)
+    for c in rng.integers(0, p.n, 6):
+        want = orc.cone(q0s[big].astype(np.int64), int(c), p.steps, p.flux, p.delta, p.dx,
+                        p.dt, a=p.a, alpha=p.alpha)
+        assert bat["results"][big][c] == want
+    one = S.serve_one_by_one(reqs, q0s)
+    for i in range(len(reqs)):
+        assert np.array_equal(bat["results"][i], one["results"][i])
+
+
+def test_batch_rejections_are_statuses():
+    p = I.burgers_problem(n=4096, steps=10)
+    q0 = F.fqnm_quantise(p.u0, p.delta)
+    b = F.fqnm_batch_create(4 << 20, 4)
+    try:
+        with pytest.raises(F.FqnmError) as e:            # larger than the budget
+            F.fqnm_batch_submit(b, F.make_spec(I.burgers_problem(n=1 << 20, steps=1)),
+                                np.zeros(1 << 20, dtype=np.int32), 1)
+        assert e.value.status == -5
+        spec = F.make_spec(p)
+        spec.boundary = 1
+        with pytest.raises(F.FqnmError) as e:            # transmissive is not served
+            F.fqnm_batch_submit(b, spec, q0, 10)
+        assert e.value.status == -1
+        spec = F.make_spec(p)
+        spec.dt = 2 * p.dx / p.alpha
+        with pytest.raises(F.FqnmError) as e:            # Courant number 2
+            F.fqnm_batch_submit(b, spec, q0, 10)
+        assert e.value.status == -2
+        rid = F.fqnm_batch_submit(b, F.make_spec(p), q0, 10)
+        while not F.fqnm_batch_completed(b, 8):
+            F.fqnm_batch_progress(b, 4)
+        q, lat = F.fqnm_batch_poll(b, rid, p.n)
+        assert q is not None and lat > 0
+        with pytest.raises(F.FqnmError) as e:            # handed out already
+            F.fqnm_batch_poll(b, rid, p.n)
+        assert e.value.status == -8
+    finally:
+        F.fqnm_batch_destroy(b)
