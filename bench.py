@@ -241,6 +241,7 @@ def run_gpu(args):
     result = None
     if rank == 0:
         baselines = fv_baselines(F, p, stream, torch) if not args.no_fv else None
+        serving = serving_block(torch) if not args.no_serving else None
         cpu = cpu_baseline(p) if (world == 1 and not args.no_cpu) else None
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -272,6 +273,8 @@ def run_gpu(args):
             result["cpu_baseline"] = cpu
         if baselines:
             result["fv_baseline"] = baselines
+        if serving:
+            result["serving"] = serving
         print(json.dumps(result))
     s.close()
     if world > 1:
@@ -311,6 +314,38 @@ def fv_baselines(F, p, stream, torch):
         out["fp%d" % prec] = {"value": n * steps / (ms / 1e3), "unit": UNIT,
                               "l1_vs_fqnm": float(p.dx * np.abs(u - u_int).sum())}
     return out
+
+
+def serving_block(torch):
+    """The batched serving path on the 4096-request stream (Poisson arrivals
+    at 2000/s, half linear advection, half Burgers, N log-uniform in
+    [256, 2^20], steps log-uniform in [100, 10^4]): online latencies and
+    throughput with the plan tuned online, the same requests all at once
+    (offline), and one problem at a time through the single-problem path."""
+    from paper_2604_06947_gb300 import serve as S
+    reqs = I.serving_stream()
+    dev = S.DeviceStream(reqs)
+    online = S.serve_batched(reqs, dev=dev, plan="autotune")
+    tuned = {k: online["plan"][k] for k in ("cells_per_thread", "block", "k", "layout")}
+    offline_reqs = [I.ServeRequest(r.rid, 0.0, r.problem, r.data_seed) for r in reqs]
+    offline = S.serve_batched(offline_reqs, dev=dev, plan=tuned)
+    out_single = torch.empty_like(dev.out)
+    one = S.serve_one_by_one(reqs, dev=dev, out=out_single)
+    identical = bool(torch.equal(out_single, dev.out))
+    keys = ("value", "p50_ms", "p99_ms", "max_ms")
+    return {
+        "workload": "4096 requests, Poisson 2000/s, half linear / half Burgers, "
+                    "N log-uniform [256, 2^20], steps log-uniform [100, 10^4], int32, delta 2^-16",
+        "cell_updates": online["cell_updates"],
+        "batched_online": dict({k: online[k] for k in keys}, makespan_s=online["makespan_s"],
+                               gpu_value=online["value_gpu"], epochs=online["epochs"],
+                               plan=tuned),
+        "batched_offline": {"value": offline["value"], "gpu_value": offline["value_gpu"],
+                            "makespan_s": offline["makespan_s"]},
+        "one_problem_at_a_time": dict({k: one[k] for k in keys}, busy_s=one["busy_s"]),
+        "results_identical": identical,
+        "unit": UNIT,
+    }
 
 
 # ---------------------------------------------------------------------------
@@ -371,6 +406,7 @@ def main():
     ap.add_argument("--impl", default="fqnm", choices=["fqnm", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fv", action="store_true", help="skip the FP finite-volume baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched serving stream")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -295,9 +295,16 @@ fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
 fqnm_status fqnm_batch_destroy(fqnm_batch* b);
 /* Execution plan of the batched launch (0 keeps a value): cells per thread
  * (4, 8, 16), threads per block, steps per epoch K, layout (1 interleaved, 2
- * blocked).  Only while no problem is active. */
+ * blocked).  Takes effect at the next epoch; results do not depend on it. */
 fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
                                 int k, int layout);
+/* Autotune the plan online: the next epochs with work try each candidate
+ * (cells per thread 8/16, 128/256 threads, K 32/64/128) for epochs_per_plan
+ * epochs, then keep the one with the least GPU time per cell update. */
+fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan);
+/* The current plan; *tuning = 1 while candidates are still being tried. */
+fqnm_status fqnm_batch_get_plan(fqnm_batch* b, int* cells_per_thread, int* block,
+                                int* k, int* layout, int* tuning);
 /* Queue a problem: q0 is a host int32 [n] (copied), `steps` time steps.
  * arrival_ns (fqnm_clock_ns clock; 0 = now) is when the request arrives: it
  * is not admitted before, and its latency is measured from it.  Validates
@@ -305,6 +312,15 @@ fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
 fqnm_status fqnm_batch_submit(fqnm_batch* b, const fqnm_problem_spec* spec,
                               const int32_t* q0, size_t n, uint64_t steps,
                               uint64_t arrival_ns, int64_t* id);
+/* Queue a problem whose initial state is already on the device: q0 is a
+ * device int32 [n] that must stay valid and unchanged until the problem has
+ * finished (it is copied at admission, and again if a range escape restarts
+ * the problem); out, if not NULL, is
+ * a device int32 [n] that receives the final state (then poll returns no
+ * host state).  The state range is taken on the GPU at admission. */
+fqnm_status fqnm_batch_submit_device(fqnm_batch* b, const fqnm_problem_spec* spec,
+                                     const int32_t* q0, size_t n, uint64_t steps,
+                                     uint64_t arrival_ns, int32_t* out, int64_t* id);
 /* Run up to max_epochs epochs (admission, one batched launch, retirement),
  * stopping early when nothing has arrived or is active.  Reports how many
  * problems are on the device and how many still wait. */
@@ -318,9 +334,10 @@ fqnm_status fqnm_batch_poll(fqnm_batch* b, int64_t id, int32_t* q_out,
 /* Pop up to max_ids tickets of problems finished since the last call (in
  * completion order) into ids; *n receives how many. */
 fqnm_status fqnm_batch_completed(fqnm_batch* b, int64_t* ids, int max_ids, int* n);
-/* Batched launches, cell updates and epochs executed so far. */
+/* Batched launches, cell updates and epochs executed so far, and the GPU
+ * time of the epochs' launches in ms (CUDA events around each epoch). */
 fqnm_status fqnm_batch_stats(fqnm_batch* b, uint64_t* launches,
-                             uint64_t* cell_updates, uint64_t* epochs);
+                             uint64_t* cell_updates, uint64_t* epochs, double* gpu_ms);
 /* The monotonic clock (ns) the batch uses for arrivals and latencies. */
 uint64_t fqnm_clock_ns(void);
 

@@ -125,7 +125,10 @@ namespace {
 
 struct Request {
     fqnm_problem_spec spec{};
-    std::vector<int32_t> q0;
+    size_t n = 0;
+    std::vector<int32_t> q0;           // host submission (copied)
+    const int32_t* q0_dev = nullptr;   // device submission (caller's)
+    int32_t* out_dev = nullptr;        // device result (caller's), else host
     std::vector<int32_t> result;
     uint64_t steps = 0;
     uint64_t arrival_ns = 0, done_ns = 0;
@@ -136,7 +139,9 @@ struct Request {
 
 struct Slot {
     int64_t req = -1;
-    size_t off = 0, bytes = 0;       // arena block
+    size_t off = 0, bytes = 0;       // arena block of the two state buffers
+    size_t toff = 0, tbytes = 0;     // arena block of the tables
+    bool range_pending = false;
     int32_t* q[2] = {nullptr, nullptr};
     int2* tab2 = nullptr;
     int32_t* tabp = nullptr;
@@ -173,18 +178,28 @@ struct fqnm_batch {
     BatchHeader* d_hdr = nullptr;
     unsigned* d_err = nullptr;
     unsigned long long* d_check = nullptr;
+    long long* d_range = nullptr;             // [2*slot]: min, max of a device submission
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double gpu_ms = 0.0;
     // pinned
     BatchDesc* h_desc = nullptr;
     long long* h_prefix = nullptr;
     BatchHeader* h_hdr = nullptr;
     unsigned* h_err = nullptr;
     unsigned long long* h_check = nullptr;
+    long long* h_range = nullptr;
     int32_t* h_stage = nullptr;
     size_t stage_ints = 0;
     // plan and graph
     Plan plan;
     int grid = 0;
     cudaGraphExec_t gexec = nullptr;
+    // online autotuning: candidate plans tried on the first epochs with work
+    bool tuning = false;
+    std::vector<Plan> cands;
+    std::vector<double> cand_ns;             // GPU ns per cell update, summed
+    std::vector<uint64_t> cand_updates;
+    int tune_epoch = 0, tune_per_plan = 3;
     // counters
     uint64_t launches = 0, cell_updates = 0, epochs = 0;
 };
@@ -198,6 +213,10 @@ static void batch_free_device(fqnm_batch* b)
     cudaFree(b->d_hdr);
     cudaFree(b->d_err);
     cudaFree(b->d_check);
+    cudaFree(b->d_range);
+    cudaFreeHost(b->h_range);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
     cudaFreeHost(b->h_desc);
     cudaFreeHost(b->h_prefix);
     cudaFreeHost(b->h_hdr);
@@ -278,6 +297,10 @@ extern "C" fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_err, max_slots * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_check, 4 * max_slots * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_stage, b->stage_ints * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_range, 2 * max_slots * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_range, 2 * max_slots * sizeof(long long));
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, max_slots * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -318,10 +341,51 @@ extern "C" fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, 
     if (!tb_plan_supported(dummy, p) || !batch_kernel(p.v, p.layout))
         return set_error(FQNM_ERR_ARG, "unsupported batch plan (V=%d, block=%d, K=%d, layout=%d)",
                          p.v, p.block, p.k, p.layout);
-    for (const Slot& s : b->slots)
-        if (s.req >= 0) return set_error(FQNM_ERR_STATE, "set the plan while no problem is active");
+    // the plan only decides how each epoch cuts problems into tiles, so it
+    // may change between epochs
     b->plan = p;
+    b->tuning = false;
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan)
+{
+    if (!b) return set_error(FQNM_ERR_ARG, "null handle");
+    if (epochs_per_plan < 1 || epochs_per_plan > 64)
+        return set_error(FQNM_ERR_ARG, "epochs_per_plan must be 1..64");
+    b->cands.clear();
+    const int vs[2] = {8, 16}, blocks[2] = {128, 256}, ks[3] = {32, 64, 128};
+    RuleView dummy{};
+    for (int v : vs)
+        for (int bl : blocks)
+            for (int k : ks) {
+                Plan p;
+                p.kernel = 2; p.layout = LAYOUT_BLOCKED; p.v = v; p.block = bl; p.k = k;
+                if (4LL * k > (long long)bl * v) continue;      // > 50 % halo work
+                if (tb_plan_supported(dummy, p)) b->cands.push_back(p);
+            }
+    b->cand_ns.assign(b->cands.size(), 0.0);
+    b->cand_updates.assign(b->cands.size(), 0);
+    b->tune_epoch = 0;
+    b->tune_per_plan = epochs_per_plan;
+    b->tuning = !b->cands.empty();
+    if (b->tuning) {
+        b->plan = b->cands[0];
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    }
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_batch_get_plan(fqnm_batch* b, int* cells_per_thread, int* block,
+                                           int* k, int* layout, int* tuning)
+{
+    if (!b) return set_error(FQNM_ERR_ARG, "null handle");
+    if (cells_per_thread) *cells_per_thread = b->plan.v;
+    if (block) *block = b->plan.block;
+    if (k) *k = b->plan.k;
+    if (layout) *layout = b->plan.layout;
+    if (tuning) *tuning = b->tuning ? 1 : 0;
     return FQNM_OK;
 }
 
@@ -332,11 +396,8 @@ static size_t problem_bytes(size_t n, int64_t count)
            align_up(count * sizeof(int32_t), 256);
 }
 
-extern "C" fqnm_status fqnm_batch_submit(fqnm_batch* b, const fqnm_problem_spec* spec,
-                                         const int32_t* q0, size_t n, uint64_t steps,
-                                         uint64_t arrival_ns, int64_t* id)
+static fqnm_status validate_spec(const fqnm_problem_spec* spec, size_t n)
 {
-    if (!b || !spec || !q0 || !id) return set_error(FQNM_ERR_ARG, "null argument");
     if (n == 0 || n > (size_t)INT32_MAX / 2) return set_error(FQNM_ERR_ARG, "bad problem size");
     if (spec->boundary != FQNM_BC_PERIODIC)
         return set_error(FQNM_ERR_ARG, "the batch serves periodic problems");
@@ -349,8 +410,19 @@ extern "C" fqnm_status fqnm_batch_submit(fqnm_batch* b, const fqnm_problem_spec*
     fqnm_status st = fqnm_create(&f, &spec->delta, spec->dx, spec->dt, spec->boundary, &probe);
     if (st != FQNM_OK) return st;
     fqnm_destroy(probe);
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_batch_submit(fqnm_batch* b, const fqnm_problem_spec* spec,
+                                         const int32_t* q0, size_t n, uint64_t steps,
+                                         uint64_t arrival_ns, int64_t* id)
+{
+    if (!b || !spec || !q0 || !id) return set_error(FQNM_ERR_ARG, "null argument");
+    fqnm_status st = validate_spec(spec, n);
+    if (st != FQNM_OK) return st;
     Request r;
     r.spec = *spec;
+    r.n = n;
     r.q0.assign(q0, q0 + n);
     r.steps = steps;
     r.arrival_ns = arrival_ns ? arrival_ns : now_ns();
@@ -367,50 +439,102 @@ extern "C" fqnm_status fqnm_batch_submit(fqnm_batch* b, const fqnm_problem_spec*
     return FQNM_OK;
 }
 
-static fqnm_status admit_one(fqnm_batch* b, int64_t rid, size_t* stage_used, bool* admitted)
+extern "C" fqnm_status fqnm_batch_submit_device(fqnm_batch* b, const fqnm_problem_spec* spec,
+                                                const int32_t* q0, size_t n, uint64_t steps,
+                                                uint64_t arrival_ns, int32_t* out,
+                                                int64_t* id)
+{
+    if (!b || !spec || !q0 || !id) return set_error(FQNM_ERR_ARG, "null argument");
+    fqnm_status st = validate_spec(spec, n);
+    if (st != FQNM_OK) return st;
+    if (problem_bytes(n, 1) > b->budget)
+        return set_error(FQNM_ERR_OOM, "problem states alone exceed the batch budget");
+    Request r;
+    r.spec = *spec;
+    r.n = n;
+    r.q0_dev = q0;
+    r.out_dev = out;
+    r.steps = steps;
+    r.arrival_ns = arrival_ns ? arrival_ns : now_ns();
+    *id = (int64_t)b->reqs.size();
+    b->reqs.push_back(std::move(r));
+    b->queue.push_back(*id);
+    return FQNM_OK;
+}
+
+// Phase 1 of admission: a slot, the state buffers and the initial state on
+// the device; a device submission also gets its state range from the GPU.
+static fqnm_status admit_state(fqnm_batch* b, int64_t rid, size_t* stage_used, bool* admitted)
 {
     *admitted = false;
     Request& r = b->reqs[rid];
-    const size_t n = r.q0.size();
-    const int64_t lo = std::max<int64_t>((int64_t)r.qmin - r.margin, INT32_MIN / 4);
-    const int64_t hi = std::min<int64_t>((int64_t)r.qmax + r.margin, INT32_MAX / 4);
-    const int64_t count = hi - lo + 1;
-    const size_t bytes = problem_bytes(n, count);
-    if (bytes > b->budget) return set_error(FQNM_ERR_OOM, "problem %lld needs %zu bytes, budget %zu",
-                                            (long long)rid, bytes, b->budget);
-    if (*stage_used + n > b->stage_ints) return FQNM_OK;          // next epoch
+    const size_t n = r.n;
+    const bool host = r.q0_dev == nullptr;
+    if (host && *stage_used + n > b->stage_ints) return FQNM_OK;          // next epoch
     if (b->free_slots.empty()) return FQNM_OK;
+    const size_t sb = align_up(n * sizeof(int32_t), 256);
     size_t off = 0;
-    if (!arena_alloc(b, bytes, &off)) return FQNM_OK;
+    if (!arena_alloc(b, 2 * sb, &off)) return FQNM_OK;
     const int si = b->free_slots.back();
     b->free_slots.pop_back();
     Slot& s = b->slots[si];
     s = Slot();
     s.req = rid;
     s.off = off;
-    s.bytes = bytes;
-    char* base = b->arena + off;
-    const size_t sb = align_up(n * sizeof(int32_t), 256);
-    s.q[0] = (int32_t*)base;
-    s.q[1] = (int32_t*)(base + sb);
-    s.tab2 = (int2*)(base + 2 * sb);
-    s.tabp = (int32_t*)(base + 2 * sb + align_up(count * sizeof(int2), 256));
+    s.bytes = 2 * sb;
+    s.q[0] = (int32_t*)(b->arena + off);
+    s.q[1] = (int32_t*)(b->arena + off + sb);
+    if (host) {
+        int32_t* stage = b->h_stage + *stage_used;
+        std::memcpy(stage, r.q0.data(), n * sizeof(int32_t));
+        *stage_used += n;
+        BCK(cudaMemcpyAsync(s.q[0], stage, n * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
+    } else {
+        BCK(cudaMemcpyAsync(s.q[0], r.q0_dev, n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                            b->stream));
+        init_minmax(b->h_range + 2 * si);
+        BCK(cudaMemcpyAsync(b->d_range + 2 * si, b->h_range + 2 * si, 2 * sizeof(long long),
+                            cudaMemcpyHostToDevice, b->stream));
+        BCK(launch_minmax_i32(s.q[0], (int64_t)n, b->d_range + 2 * si, b->stream));
+        s.range_pending = true;
+    }
+    r.state = 1;
+    *admitted = true;
+    return FQNM_OK;
+}
+
+// Phase 2: the transfer tables over the state range, built and checked on
+// the GPU.  False in *ok if the arena has no room yet (the caller requeues).
+static fqnm_status admit_table(fqnm_batch* b, int si, bool* ok)
+{
+    *ok = false;
+    Slot& s = b->slots[si];
+    Request& r = b->reqs[s.req];
+    const int64_t lo = std::max<int64_t>((int64_t)r.qmin - r.margin, INT32_MIN / 4);
+    const int64_t hi = std::min<int64_t>((int64_t)r.qmax + r.margin, INT32_MAX / 4);
+    const int64_t count = hi - lo + 1;
+    if (problem_bytes(r.n, count) > b->budget)
+        return set_error(FQNM_ERR_OOM, "problem %lld needs %zu bytes, the batch budget is %zu",
+                         (long long)s.req, problem_bytes(r.n, count), b->budget);
+    const size_t t2 = align_up(count * sizeof(int2), 256);
+    const size_t tb = t2 + align_up(count * sizeof(int32_t), 256);
+    size_t toff = 0;
+    if (!arena_alloc(b, tb, &toff)) return FQNM_OK;
+    s.toff = toff;
+    s.tbytes = tb;
+    s.tab2 = (int2*)(b->arena + toff);
+    s.tabp = (int32_t*)(b->arena + toff + t2);
     s.lo = (int32_t)lo;
     s.span = (uint32_t)(count - 1);
     const fqnm_flux& f = r.spec.flux;
     s.has_m = !(f.kind == FQNM_FLUX_LINEAR_UPWIND && f.a >= 0.0);
     s.evaluator = EVAL_TABLE;
-    // stage the initial state and upload it
-    int32_t* stage = b->h_stage + *stage_used;
-    std::memcpy(stage, r.q0.data(), n * sizeof(int32_t));
-    *stage_used += n;
-    BCK(cudaMemcpyAsync(s.q[0], stage, n * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemsetAsync(b->d_err + si, 0, sizeof(unsigned), b->stream));
     BCK(launch_build_split_table(f.kind, f.a, f.alpha, r.spec.delta, r.spec.dt / r.spec.dx,
                                  f.rounding, lo, count, s.tab2, s.tabp, b->d_err + si, b->stream));
-    // certificate, phi- presence and (for a linear map) the closed form 1/den
-    // candidates are checked on the GPU; the table is used until the result
-    // is read back at the end of the epoch
+    // certificate, phi- presence and, for a linear map, one closed-form
+    // candidate are checked on the GPU; the table serves until the result is
+    // read back at the end of the epoch
     BCK(cudaMemsetAsync(b->d_check + 4 * si, 0, 4 * sizeof(unsigned long long), b->stream));
     ClosedForm cf{};
     bool cand = false;
@@ -425,8 +549,7 @@ static fqnm_status admit_one(fqnm_batch* b, int64_t rid, size_t* stage_used, boo
     s.cf = cf;
     s.cf_candidate = cand;
     s.check_pending = true;
-    r.state = 1;
-    *admitted = true;
+    *ok = true;
     return FQNM_OK;
 }
 
@@ -434,6 +557,8 @@ static void release_slot(fqnm_batch* b, int si)
 {
     Slot& s = b->slots[si];
     arena_free(b, s.off, s.bytes);
+    if (s.tbytes) arena_free(b, s.toff, s.tbytes);
+    s.tbytes = 0;
     s.req = -1;
     b->free_slots.push_back(si);
 }
@@ -475,17 +600,53 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
 {
     *did_work = false;
     const uint64_t t = now_ns();
-    // 1. admission
+    // 1. admission: states first, then (after one sync if a device
+    // submission needs its range) the tables
     size_t stage_used = 0;
+    std::vector<int> fresh;
+    bool need_range = false;
     for (auto it = b->queue.begin(); it != b->queue.end();) {
         Request& r = b->reqs[*it];
         if (r.arrival_ns > t) { ++it; continue; }
         bool adm = false;
-        fqnm_status st = admit_one(b, *it, &stage_used, &adm);
+        const int64_t rid = *it;
+        fqnm_status st = admit_state(b, rid, &stage_used, &adm);
         if (st != FQNM_OK) return st;
-        if (adm) it = b->queue.erase(it);
-        else ++it;
+        if (adm) {
+            it = b->queue.erase(it);
+            for (int si = 0; si < b->max_slots; ++si)
+                if (b->slots[si].req == rid && !b->slots[si].tbytes) {
+                    fresh.push_back(si);
+                    need_range = need_range || b->slots[si].range_pending;
+                    break;
+                }
+        } else {
+            ++it;
+        }
         if (b->free_slots.empty()) break;
+    }
+    if (need_range) {
+        BCK(cudaMemcpyAsync(b->h_range, b->d_range, 2 * b->max_slots * sizeof(long long),
+                            cudaMemcpyDeviceToHost, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+    }
+    for (int si : fresh) {
+        Slot& s = b->slots[si];
+        Request& r = b->reqs[s.req];
+        if (s.range_pending) {
+            r.qmin = (int32_t)b->h_range[2 * si];
+            r.qmax = (int32_t)b->h_range[2 * si + 1];
+            s.range_pending = false;
+        }
+        bool ok = false;
+        fqnm_status st = admit_table(b, si, &ok);
+        if (st != FQNM_OK) return st;
+        if (!ok) {                                    // no room for the tables yet
+            const int64_t rid = s.req;
+            r.state = 0;
+            release_slot(b, si);
+            b->queue.push_front(rid);
+        }
     }
     // 2. the epoch's launch over every active problem with steps left
     const long long E = (long long)b->plan.block * b->plan.v;
@@ -499,7 +660,7 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
         if (s.done >= r.steps) continue;
         const int k = (int)std::min<uint64_t>((uint64_t)b->plan.k, r.steps - s.done);
         const long long S = E - 2LL * k;
-        const long long n = (long long)r.q0.size();
+        const long long n = (long long)r.n;
         BatchDesc& d = b->h_desc[np];
         d.qin = s.q[s.cur];
         d.qout = s.q[1 - s.cur];
@@ -527,7 +688,9 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
             fqnm_status st = build_epoch_graph(b);
             if (st != FQNM_OK) return st;
         }
+        BCK(cudaEventRecord(b->ev0, b->stream));
         BCK(cudaGraphLaunch(b->gexec, b->stream));
+        BCK(cudaEventRecord(b->ev1, b->stream));
         note_launches();
         b->launches += 1;
         b->epochs += 1;
@@ -543,14 +706,18 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
         if (s.k_this_epoch) {
             s.done += s.k_this_epoch;
             s.cur = 1 - s.cur;
-            b->cell_updates += (uint64_t)s.k_this_epoch * r.q0.size();
+            b->cell_updates += (uint64_t)s.k_this_epoch * r.n;
         }
-        if (s.done >= r.steps && out_used + r.q0.size() <= b->stage_ints) {
-            BCK(cudaMemcpyAsync(b->h_stage + out_used, s.q[s.cur], r.q0.size() * sizeof(int32_t),
+        if (s.done >= r.steps && r.out_dev) {
+            BCK(cudaMemcpyAsync(r.out_dev, s.q[s.cur], r.n * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, b->stream));
+            finished.push_back(si);
+        } else if (s.done >= r.steps && out_used + r.n <= b->stage_ints) {
+            BCK(cudaMemcpyAsync(b->h_stage + out_used, s.q[s.cur], r.n * sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, b->stream));
             finished.push_back(si);
             s.out_off = out_used;
-            out_used += r.q0.size();
+            out_used += r.n;
         }
         *did_work = *did_work || s.req >= 0;
     }
@@ -560,6 +727,37 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
                         cudaMemcpyDeviceToHost, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
     const uint64_t tdone = now_ns();
+    if (np > 0) {
+        float ms = 0.0f;
+        BCK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        b->gpu_ms += ms;
+        if (b->tuning) {
+            uint64_t upd = 0;
+            for (int i = 0; i < np; ++i) upd += (uint64_t)b->h_desc[i].n * b->h_desc[i].k;
+            const size_t c = (size_t)(b->tune_epoch / b->tune_per_plan);
+            b->cand_ns[c] += 1e6 * ms;
+            b->cand_updates[c] += upd;
+            ++b->tune_epoch;
+            const size_t nc = (size_t)(b->tune_epoch / b->tune_per_plan);
+            if (nc >= b->cands.size()) {           // all tried: keep the fastest
+                size_t best = 0;
+                double best_v = 1e300;
+                for (size_t j = 0; j < b->cands.size(); ++j) {
+                    if (!b->cand_updates[j]) continue;
+                    const double v = b->cand_ns[j] / (double)b->cand_updates[j];
+                    if (v < best_v) { best_v = v; best = j; }
+                }
+                b->plan = b->cands[best];
+                b->tuning = false;
+            } else if (nc != c) {
+                b->plan = b->cands[nc];
+            }
+            if (b->gexec && (nc != c || !b->tuning)) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+        }
+    }
     // rule checks of newly admitted problems
     for (int si = 0; si < b->max_slots; ++si) {
         Slot& s = b->slots[si];
@@ -587,7 +785,7 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
     for (int si : finished) {
         Slot& s = b->slots[si];
         Request& r = b->reqs[s.req];
-        r.result.assign(b->h_stage + s.out_off, b->h_stage + s.out_off + r.q0.size());
+        if (!r.out_dev) r.result.assign(b->h_stage + s.out_off, b->h_stage + s.out_off + r.n);
         r.done_ns = tdone;
         r.state = 2;
         b->completed.push_back(s.req);
@@ -620,7 +818,7 @@ extern "C" fqnm_status fqnm_batch_poll(fqnm_batch* b, int64_t id, int32_t* q_out
     *done = 0;
     if (r.state == 3) return set_error(FQNM_ERR_STATE, "result %lld already handed out", (long long)id);
     if (r.state != 2) return FQNM_OK;
-    if (q_out) std::memcpy(q_out, r.result.data(), r.result.size() * sizeof(int32_t));
+    if (q_out && !r.out_dev) std::memcpy(q_out, r.result.data(), r.result.size() * sizeof(int32_t));
     if (latency_ns) *latency_ns = r.done_ns - r.arrival_ns;
     *done = 1;
     r.state = 3;
@@ -643,11 +841,13 @@ extern "C" fqnm_status fqnm_batch_completed(fqnm_batch* b, int64_t* ids, int max
 }
 
 extern "C" fqnm_status fqnm_batch_stats(fqnm_batch* b, uint64_t* launches,
-                                        uint64_t* cell_updates, uint64_t* epochs)
+                                        uint64_t* cell_updates, uint64_t* epochs,
+                                        double* gpu_ms)
 {
     if (!b) return set_error(FQNM_ERR_ARG, "null handle");
     if (launches) *launches = b->launches;
     if (cell_updates) *cell_updates = b->cell_updates;
     if (epochs) *epochs = b->epochs;
+    if (gpu_ms) *gpu_ms = b->gpu_ms;
     return FQNM_OK;
 }

@@ -111,13 +111,17 @@ PROTOTYPES = {
     "fqnm_batch_create": (_st, [C.c_size_t, C.c_int, _vp, C.POINTER(_vp)]),
     "fqnm_batch_destroy": (_st, [_vp]),
     "fqnm_batch_set_plan": (_st, [_vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "fqnm_batch_autotune": (_st, [_vp, C.c_int]),
+    "fqnm_batch_get_plan": (_st, [_vp] + [C.POINTER(C.c_int)] * 5),
     "fqnm_batch_submit": (_st, [_vp, C.POINTER(fqnm_problem_spec), _vp, C.c_size_t,
                                 C.c_uint64, C.c_uint64, C.POINTER(C.c_int64)]),
     "fqnm_batch_progress": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fqnm_batch_poll": (_st, [_vp, C.c_int64, _vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
     "fqnm_batch_completed": (_st, [_vp, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int)]),
+    "fqnm_batch_submit_device": (_st, [_vp, C.POINTER(fqnm_problem_spec), _vp, C.c_size_t,
+                                       C.c_uint64, C.c_uint64, _vp, C.POINTER(C.c_int64)]),
     "fqnm_batch_stats": (_st, [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
-                               C.POINTER(C.c_uint64)]),
+                               C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
     "fqnm_clock_ns": (C.c_uint64, []),
     "fqnm_last_error": (C.c_char_p, []),
     "fqnm_status_string": (C.c_char_p, [C.c_int]),
@@ -397,12 +401,30 @@ def fqnm_batch_set_plan(b: int, cells_per_thread: int = 0, block: int = 0, k: in
     _check(load().fqnm_batch_set_plan(b, cells_per_thread, block, k, layout))
 
 
+def fqnm_batch_autotune(b: int, epochs_per_plan: int = 3):
+    _check(load().fqnm_batch_autotune(b, epochs_per_plan))
+
+
+def fqnm_batch_get_plan(b: int) -> dict:
+    v = [C.c_int(0) for _ in range(5)]
+    _check(load().fqnm_batch_get_plan(b, *[C.byref(x) for x in v]))
+    return dict(zip(("cells_per_thread", "block", "k", "layout", "tuning"), [x.value for x in v]))
+
+
 def fqnm_batch_submit(b: int, spec: fqnm_problem_spec, q0, steps: int,
                       arrival_ns: int = 0) -> int:
     q = np.ascontiguousarray(q0, dtype=np.int32)
     rid = C.c_int64(0)
     _check(load().fqnm_batch_submit(b, C.byref(spec), q.ctypes.data, q.shape[0], steps,
                                     arrival_ns, C.byref(rid)))
+    return rid.value
+
+
+def fqnm_batch_submit_device(b: int, spec: fqnm_problem_spec, q0_dev, n: int, steps: int,
+                             arrival_ns: int = 0, out_dev=None) -> int:
+    rid = C.c_int64(0)
+    _check(load().fqnm_batch_submit_device(b, C.byref(spec), _dptr(q0_dev), n, steps,
+                                           arrival_ns, _dptr(out_dev) or None, C.byref(rid)))
     return rid.value
 
 
@@ -428,9 +450,10 @@ def fqnm_batch_completed(b: int, max_ids: int = 4096):
 
 
 def fqnm_batch_stats(b: int) -> dict:
-    l, c, e = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0)
-    _check(load().fqnm_batch_stats(b, C.byref(l), C.byref(c), C.byref(e)))
-    return {"launches": l.value, "cell_updates": c.value, "epochs": e.value}
+    l, c, e, g = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0), C.c_double(0)
+    _check(load().fqnm_batch_stats(b, C.byref(l), C.byref(c), C.byref(e), C.byref(g)))
+    return {"launches": l.value, "cell_updates": c.value, "epochs": e.value,
+            "gpu_ms": g.value}
 
 
 def fqnm_clock_ns() -> int:

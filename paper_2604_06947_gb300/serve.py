@@ -28,23 +28,58 @@ def prepare(requests: List[I.ServeRequest]) -> List[np.ndarray]:
     return out
 
 
+class DeviceStream:
+    """Initial states of a whole request stream resident on the GPU (one int32
+    buffer, problem i at offs[i]), and a buffer for the final states."""
+
+    def __init__(self, requests: List[I.ServeRequest]):
+        import torch
+        self.ns = np.array([rq.problem.n for rq in requests], dtype=np.int64)
+        self.offs = np.concatenate([[0], np.cumsum(self.ns)[:-1]])
+        total = int(self.ns.sum())
+        self.q = torch.empty(total, dtype=torch.int32, device="cuda")
+        self.out = torch.empty(total, dtype=torch.int32, device="cuda")
+        for i, rq in enumerate(requests):
+            p = I.materialise(rq)
+            u = torch.from_numpy(p.u0).cuda()
+            F.fqnm_quantise_device(u, p.n, p.delta, self.q_ptr(i))
+            p.u0 = None
+        torch.cuda.synchronize()
+
+    def q_ptr(self, i: int) -> int:
+        return self.q.data_ptr() + 4 * int(self.offs[i])
+
+    def out_ptr(self, i: int) -> int:
+        return self.out.data_ptr() + 4 * int(self.offs[i])
+
+    def q0(self, i: int):
+        return self.q[int(self.offs[i]):int(self.offs[i] + self.ns[i])]
+
+    def result(self, i: int):
+        return self.out[int(self.offs[i]):int(self.offs[i] + self.ns[i])]
+
+
 def _percentiles(lat_ns: np.ndarray) -> Dict[str, float]:
     return {"p50_ms": float(np.percentile(lat_ns, 50) / 1e6),
             "p99_ms": float(np.percentile(lat_ns, 99) / 1e6),
             "max_ms": float(lat_ns.max() / 1e6)}
 
 
-def serve_batched(requests: List[I.ServeRequest], q0s: List[np.ndarray],
+def serve_batched(requests: List[I.ServeRequest], q0s=None,
                   budget_bytes: int = 16 << 30, max_slots: int = 1024,
                   plan: Optional[dict] = None, keep: Optional[set] = None,
-                  lead_s: float = 0.02) -> dict:
+                  lead_s: float = 0.02, dev: Optional[DeviceStream] = None) -> dict:
     """Run the stream through one batch in real time.
 
-    keep: request indices whose final states are returned (all if None).
+    q0s: host initial states (host submission), or dev: a DeviceStream whose
+    initial and final states stay on the GPU (device submission).
+    keep: request indices whose host final states are returned (all if None).
     """
     b = F.fqnm_batch_create(budget_bytes, max_slots)
     try:
-        if plan:
+        if plan == "autotune":
+            F.fqnm_batch_autotune(b, 3)
+        elif plan:
             F.fqnm_batch_set_plan(b, **plan)
         specs = [F.make_spec(rq.problem) for rq in requests]
         order = sorted(range(len(requests)), key=lambda i: requests[i].arrival_s)
@@ -60,7 +95,14 @@ def serve_batched(requests: List[I.ServeRequest], q0s: List[np.ndarray],
                 t_arr = t0 + int(requests[i].arrival_s * 1e9)
                 if t_arr > now:
                     break
-                rid = F.fqnm_batch_submit(b, specs[i], q0s[i], requests[i].problem.steps, t_arr)
+                if dev is None:
+                    rid = F.fqnm_batch_submit(b, specs[i], q0s[i], requests[i].problem.steps,
+                                              t_arr)
+                else:
+                    rid = F.fqnm_batch_submit_device(b, specs[i], dev.q_ptr(i),
+                                                     requests[i].problem.n,
+                                                     requests[i].problem.steps, t_arr,
+                                                     dev.out_ptr(i))
                 id2req[rid] = i
                 nxt += 1
             active, queued = F.fqnm_batch_progress(b, 1)
@@ -68,7 +110,7 @@ def serve_batched(requests: List[I.ServeRequest], q0s: List[np.ndarray],
                 i = id2req[rid]
                 q, l = F.fqnm_batch_poll(b, rid, requests[i].problem.n)
                 lat[i] = l
-                if keep is None or i in keep:
+                if dev is None and (keep is None or i in keep):
                     results[i] = q
                 done += 1
                 t_last = F.fqnm_clock_ns()
@@ -77,22 +119,27 @@ def serve_batched(requests: List[I.ServeRequest], q0s: List[np.ndarray],
                 if wait > 0:
                     time.sleep(min(wait, 0.001))
         stats = F.fqnm_batch_stats(b)
+        final_plan = F.fqnm_batch_get_plan(b)
     finally:
         F.fqnm_batch_destroy(b)
     work = sum(rq.problem.n * rq.problem.steps for rq in requests)
     makespan = (t_last - t0) / 1e9
     out = {"requests": len(requests), "cell_updates": work,
            "makespan_s": makespan, "value": work / makespan,
+           "gpu_s": stats["gpu_ms"] / 1e3, "value_gpu": work / (stats["gpu_ms"] / 1e3),
            "launches": stats["launches"], "epochs": stats["epochs"],
-           "latency_ns": lat, "results": results}
+           "plan": final_plan, "latency_ns": lat, "results": results}
     out.update(_percentiles(lat))
     return out
 
 
-def serve_one_by_one(requests: List[I.ServeRequest], q0s: List[np.ndarray],
-                     keep: Optional[set] = None) -> dict:
+def serve_one_by_one(requests: List[I.ServeRequest], q0s=None,
+                     keep: Optional[set] = None, dev: Optional[DeviceStream] = None,
+                     out=None) -> dict:
     """Each problem alone through the single-problem path, in arrival order;
-    latencies from a FIFO queue over the measured service times."""
+    latencies from a FIFO queue over the measured service times.  With dev,
+    states are loaded from and returned to device memory (out: a device
+    int32 buffer laid out like dev.out)."""
     order = sorted(range(len(requests)), key=lambda i: requests[i].arrival_s)
     service = np.zeros(len(requests))
     results: Dict[int, np.ndarray] = {}
@@ -100,11 +147,17 @@ def serve_one_by_one(requests: List[I.ServeRequest], q0s: List[np.ndarray],
         p = requests[i].problem
         t = time.perf_counter()
         s = F.Solver.for_problem(p)
-        s.load(q0s[i]).step(p.steps)
-        q = s.state()
+        if dev is None:
+            s.load(q0s[i]).step(p.steps)
+            q = s.state()
+        else:
+            s.load_device(dev.q_ptr(i), p.n).step(p.steps)
+            F.fqnm_checkpoint_device(s.h, out.data_ptr() + 4 * int(dev.offs[i]))
+            F.fqnm_sync(s.h)
+            q = None
         s.close()
         service[i] = time.perf_counter() - t
-        if keep is None or i in keep:
+        if q is not None and (keep is None or i in keep):
             results[i] = q
     finish, lat = 0.0, np.zeros(len(requests), dtype=np.int64)
     for i in order:

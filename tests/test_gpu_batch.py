@@ -52,6 +52,30 @@ def test_every_batch_plan_gives_the_same_results(plan):
         assert np.array_equal(bat["results"][i], ref["results"][i]), (plan, i)
 
 
+def test_online_autotune_keeps_results():
+    reqs = small_stream(n_requests=40, seed=12)
+    q0s = S.prepare(reqs)
+    ref = S.serve_one_by_one(reqs, q0s)
+    bat = S.serve_batched(reqs, q0s, budget_bytes=64 << 20, max_slots=8, plan="autotune")
+    for i in range(len(reqs)):
+        assert np.array_equal(bat["results"][i], ref["results"][i]), i
+    assert bat["plan"]["cells_per_thread"] in (8, 16)
+
+
+def test_device_submission_and_device_results(orc):
+    import torch
+    reqs = small_stream(n_requests=20, seed=14)
+    dev = S.DeviceStream(reqs)
+    S.serve_batched(reqs, dev=dev, budget_bytes=32 << 20, max_slots=4)
+    out = torch.empty_like(dev.out)
+    S.serve_one_by_one(reqs, dev=dev, out=out)
+    assert torch.equal(out, dev.out)
+    p = reqs[5].problem
+    want = orc.step(dev.q0(5).cpu().numpy(), p.flux, p.delta, p.dx, p.dt, p.steps, a=p.a,
+                    alpha=p.alpha)
+    assert np.array_equal(dev.result(5).cpu().numpy().astype(np.int64), want)
+
+
 def test_large_problems_in_the_mix(orc):
     """Problems up to 2^20 cells next to small ones (sampled cells checked
     against the oracle's dependency cones)."""
