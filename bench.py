@@ -242,6 +242,7 @@ def run_gpu(args):
     if rank == 0:
         baselines = fv_baselines(F, p, stream, torch) if not args.no_fv else None
         serving = serving_block(torch) if not args.no_serving else None
+        workloads = other_workloads(F, torch, stream) if not args.no_workloads else None
         cpu = cpu_baseline(p) if (world == 1 and not args.no_cpu) else None
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -275,6 +276,8 @@ def run_gpu(args):
             result["fv_baseline"] = baselines
         if serving:
             result["serving"] = serving
+        if workloads:
+            result["workloads"] = workloads
         print(json.dumps(result))
     s.close()
     if world > 1:
@@ -313,6 +316,87 @@ def fv_baselines(F, p, stream, torch):
         F.fqnm_fv_destroy(h)
         out["fp%d" % prec] = {"value": n * steps / (ms / 1e3), "unit": UNIT,
                               "l1_vs_fqnm": float(p.dx * np.abs(u - u_int).sum())}
+    return out
+
+
+def _timed(stream, torch, fn, reps):
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return statistics.median(ts)
+
+
+def other_workloads(F, torch, stream):
+    """The other workloads of the path, each timed on the device (median of
+    3), with inputs resident on the GPU:
+      - high-frequency transport, 2^24 cells, upwind nu = 0.9, 2000 steps
+        (the verified closed form 9/10 replaces the table);
+      - linear advection, 1024 cells, 2000 steps (a latency case);
+      - Sod, 2^16 cells, componentwise-quantised Roe, to t = 0.2, and the
+        FP64 Roe finite-volume baseline on the same grid."""
+    peak, _ = measured_peak()
+    out = {}
+    for name, make in (("high_frequency_16m", I.high_frequency_problem),
+                       ("linear_advection_1k", I.linear_advection_problem)):
+        p = make()
+        u0 = torch.from_numpy(p.u0).cuda()
+        s = F.Solver.for_problem(p, autotune=1)
+        F.fqnm_set_stream(s.h, stream)
+        s.load_field(u0, p.n, on_device=True)
+        st = F.fqnm_get_stats(s.h)
+
+        def run():
+            F.fqnm_load_field(s.h, u0, p.n, on_device=True)
+            F.fqnm_step(s.h, p.steps)
+        with torch.cuda.stream(stream):
+            run()
+            t = _timed(stream, torch, run, 3)
+        F.fqnm_sync(s.h)
+        rule = F.fqnm_get_rule(s.h)
+        eff = BYTES_PER_UPDATE * p.n * p.steps / t / 1e9
+        out[name] = {"n_cells": p.n, "time_steps": p.steps, "seconds": t,
+                     "value": p.n * p.steps / t, "unit": UNIT,
+                     "effective_GBps": eff, "frac_of_hbm_peak": eff / peak,
+                     "map": "closed form %d/%d" % (rule["num"], rule["den"])
+                     if rule["evaluator"] == 2 else "table",
+                     "plan": {k: st[k] for k in ("layout", "cells_per_thread", "block", "k")}}
+        s.close()
+    # Sod: integer Roe and the FP64 Roe FV baseline
+    p = I.sod_problem(n=1 << 16)
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive")
+    F.fqnm_set_stream(s.h, stream)
+    U0 = torch.from_numpy(p.U0.reshape(-1).copy()).cuda()
+    with torch.cuda.stream(stream):
+        s.load_field(U0, p.n, on_device=True)
+        t_int = _timed(stream, torch, lambda: (F.fqnm_load_field(s.h, U0, p.n, on_device=True),
+                                               F.fqnm_step(s.h, p.steps)), 1)
+    inv = F.fqnm_invariants(s.h)
+    u = s.observe()
+    s.close()
+    fv = F.fqnm_fv_create(F.make_flux("euler_roe", gamma=p.gamma), p.dx, p.dt, "transmissive", 64)
+    F.fqnm_fv_set_stream(fv, stream)
+    with torch.cuda.stream(stream):
+        F.fqnm_fv_load_device(fv, U0, p.n)
+        t_fv = _timed(stream, torch, lambda: (F.fqnm_fv_load_device(fv, U0, p.n),
+                                              F.fqnm_fv_step(fv, p.steps)), 1)
+    ufv = F.fqnm_fv_observe(fv, p.n, 3)
+    F.fqnm_fv_destroy(fv)
+    q0 = [int(round(v)) for v in (p.U0.sum(axis=1) / np.array(p.delta))]
+    out["sod_65k"] = {
+        "n_cells": p.n, "time_steps": p.steps, "t_end": 0.2,
+        "seconds": t_int, "face_evaluations_per_s": (p.n + 1) * p.steps / t_int,
+        "fv64_roe_seconds": t_fv,
+        "l1_density_integer_vs_fv64": float(p.dx * np.abs(u[0] - ufv[0]).sum()),
+        "totals_balance_exact": all(inv["mass"][k] == q0[k] - inv["boundary_flux"][k]
+                                    for k in range(3)),
+        "bound": "fp64 pipe (Roe flux, about 100 FP64 operations per face)",
+    }
     return out
 
 
@@ -407,6 +491,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fv", action="store_true", help="skip the FP finite-volume baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched serving stream")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other workloads (high-frequency 16M, linear 1k, Sod)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

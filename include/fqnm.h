@@ -123,14 +123,17 @@ fqnm_status fqnm_set_stream(fqnm_solver* s, void* stream);
 typedef enum {
     FQNM_OPT_KERNEL = 0,     /* 0 auto, 1 naive one-step, 2 temporal-blocked */
     FQNM_OPT_LAYOUT = 1,     /* 0 auto, 1 interleaved, 2 blocked (cells per thread contiguous) */
-    FQNM_OPT_CELLS_PER_THREAD = 2, /* 4, 8 or 16; 0 auto */
-    FQNM_OPT_BLOCK = 3,      /* threads per block, multiple of 32, <= 1024; 0 auto */
+    FQNM_OPT_CELLS_PER_THREAD = 2, /* 4, 8, 16 or 32; 0 auto */
+    FQNM_OPT_BLOCK = 3,      /* threads per block, multiple of 32, <= 512 (32: one warp, no barrier); 0 auto */
     FQNM_OPT_K = 4,          /* time steps per launch (temporal block depth); 0 auto */
     FQNM_OPT_MARGIN = 5,     /* quanta added on each side of the loaded range (default 1024) */
     FQNM_OPT_CLOSED_FORM = 6,/* 1 (default): use a verified integer closed form when one exists */
     FQNM_OPT_RECOVER = 7,    /* 1 (default): on range escape widen the map and replay */
     FQNM_OPT_AUTOTUNE = 8,   /* 1: time candidate plans at load and keep the fastest */
-    FQNM_OPT_GRAPH = 9       /* 1 (default): replay long step loops from a CUDA graph */
+    FQNM_OPT_GRAPH = 9,      /* 1 (default): replay long step loops from a CUDA graph */
+    FQNM_OPT_PDL = 10        /* 1 (default): chain step launches with programmatic dependent
+                                launch (the next launch's blocks start while the previous
+                                drains, and wait for its results before reading them) */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 
@@ -222,6 +225,10 @@ fqnm_status fqnm_invariants_noalloc(const int32_t* q, const int32_t* other,
                                     size_t n, int boundary, int64_t* out,
                                     void* stream);
 
+/* Number of cells and of conserved variables of the loaded state (0 cells
+ * before the first load). */
+fqnm_status fqnm_get_size(fqnm_solver* s, size_t* n_cells, int* nvars);
+
 /* Description of the transfer rule built at load (eq. flux_table). */
 typedef struct {
     int64_t lo, hi;        /* q range the maps are tabulated and verified on */
@@ -270,6 +277,8 @@ fqnm_status fqnm_fv_step(fqnm_fv* f, uint64_t k);
 fqnm_status fqnm_fv_observe(fqnm_fv* f, double* u_out);          /* host, syncs */
 fqnm_status fqnm_fv_observe_device(fqnm_fv* f, double* u_out);   /* device */
 fqnm_status fqnm_fv_launches(fqnm_fv* f, uint64_t* launches);
+/* Cells and variables of the loaded field (0 cells before the first load). */
+fqnm_status fqnm_fv_get_size(fqnm_fv* f, size_t* n_cells, int* nvars);
 
 /* ---- batched serving ------------------------------------------------------ */
 
@@ -326,11 +335,13 @@ fqnm_status fqnm_batch_submit_device(fqnm_batch* b, const fqnm_problem_spec* spe
  * problems are on the device and how many still wait. */
 fqnm_status fqnm_batch_progress(fqnm_batch* b, int max_epochs, int* n_active,
                                 int* n_queued);
-/* If problem `id` is finished: copy its final state to q_out (host int32 [n],
- * may be NULL), its arrival-to-result latency in ns, set *done = 1 and
- * release the result (a second poll is FQNM_ERR_STATE).  Else *done = 0. */
+/* If problem `id` is finished: copy its final state to q_out (host int32,
+ * room for `capacity` values, at least the problem's n; may be NULL), its
+ * arrival-to-result latency in ns, set *done = 1 and release the result (a
+ * second poll is FQNM_ERR_STATE).  Else *done = 0.  A capacity below n is
+ * FQNM_ERR_ARG and releases nothing. */
 fqnm_status fqnm_batch_poll(fqnm_batch* b, int64_t id, int32_t* q_out,
-                            uint64_t* latency_ns, int* done);
+                            size_t capacity, uint64_t* latency_ns, int* done);
 /* Pop up to max_ids tickets of problems finished since the last call (in
  * completion order) into ids; *n receives how many. */
 fqnm_status fqnm_batch_completed(fqnm_batch* b, int64_t* ids, int max_ids, int* n);

@@ -55,7 +55,7 @@ struct BatchHeader {
     long long total_tiles;
 };
 
-template <int V, int LAYOUT>
+template <int V, int LAYOUT, bool WARP>
 __global__ void __launch_bounds__(tb::TB_MAX_BLOCK)
 k_batch_step(const BatchDesc* __restrict__ d, const long long* __restrict__ prefix,
              const BatchHeader* __restrict__ hdr)
@@ -73,13 +73,13 @@ k_batch_step(const BatchDesc* __restrict__ d, const long long* __restrict__ pref
         const long long tile = t - prefix[lo];
         if (D.evaluator == EVAL_CLOSED_FORM) {
             tb::EvClosedP ev{D.cf, D.lo, D.span};
-            tb::tile_step<tb::EvClosedP, V, LAYOUT>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
+            tb::tile_step<tb::EvClosedP, V, LAYOUT, WARP>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
         } else if (!D.has_m) {
             tb::EvTableP ev{D.tabp, D.lo, D.span};
-            tb::tile_step<tb::EvTableP, V, LAYOUT>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
+            tb::tile_step<tb::EvTableP, V, LAYOUT, WARP>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
         } else {
             tb::EvTablePM ev{D.tab2, D.lo, D.span};
-            tb::tile_step<tb::EvTablePM, V, LAYOUT>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
+            tb::tile_step<tb::EvTablePM, V, LAYOUT, WARP>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
         }
         __syncthreads();                              // shared edges are reused by the next tile
     }
@@ -87,16 +87,17 @@ k_batch_step(const BatchDesc* __restrict__ d, const long long* __restrict__ pref
 
 using BatchKernel = void (*)(const BatchDesc*, const long long*, const BatchHeader*);
 
-BatchKernel batch_kernel(int v, int layout)
+BatchKernel batch_kernel(int v, int layout, int block)
 {
+    const bool w = block == 32;
     if (layout == LAYOUT_BLOCKED) {
-        if (v == 4) return k_batch_step<4, LAYOUT_BLOCKED>;
-        if (v == 8) return k_batch_step<8, LAYOUT_BLOCKED>;
-        if (v == 16) return k_batch_step<16, LAYOUT_BLOCKED>;
+        if (v == 4) return w ? k_batch_step<4, LAYOUT_BLOCKED, true> : k_batch_step<4, LAYOUT_BLOCKED, false>;
+        if (v == 8) return w ? k_batch_step<8, LAYOUT_BLOCKED, true> : k_batch_step<8, LAYOUT_BLOCKED, false>;
+        if (v == 16) return w ? k_batch_step<16, LAYOUT_BLOCKED, true> : k_batch_step<16, LAYOUT_BLOCKED, false>;
     } else {
-        if (v == 4) return k_batch_step<4, LAYOUT_INTERLEAVED>;
-        if (v == 8) return k_batch_step<8, LAYOUT_INTERLEAVED>;
-        if (v == 16) return k_batch_step<16, LAYOUT_INTERLEAVED>;
+        if (v == 4) return w ? k_batch_step<4, LAYOUT_INTERLEAVED, true> : k_batch_step<4, LAYOUT_INTERLEAVED, false>;
+        if (v == 8) return w ? k_batch_step<8, LAYOUT_INTERLEAVED, true> : k_batch_step<8, LAYOUT_INTERLEAVED, false>;
+        if (v == 16) return w ? k_batch_step<16, LAYOUT_INTERLEAVED, true> : k_batch_step<16, LAYOUT_INTERLEAVED, false>;
     }
     return nullptr;
 }
@@ -338,7 +339,7 @@ extern "C" fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, 
     if (k) p.k = k;
     if (layout) p.layout = layout;
     RuleView dummy{};
-    if (!tb_plan_supported(dummy, p) || !batch_kernel(p.v, p.layout))
+    if (!tb_plan_supported(dummy, p) || !batch_kernel(p.v, p.layout, p.block))
         return set_error(FQNM_ERR_ARG, "unsupported batch plan (V=%d, block=%d, K=%d, layout=%d)",
                          p.v, p.block, p.k, p.layout);
     // the plan only decides how each epoch cuts problems into tiles, so it
@@ -355,7 +356,7 @@ extern "C" fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan)
     if (epochs_per_plan < 1 || epochs_per_plan > 64)
         return set_error(FQNM_ERR_ARG, "epochs_per_plan must be 1..64");
     b->cands.clear();
-    const int vs[2] = {8, 16}, blocks[2] = {128, 256}, ks[3] = {32, 64, 128};
+    const int vs[2] = {8, 16}, blocks[3] = {32, 128, 256}, ks[3] = {32, 64, 128};
     RuleView dummy{};
     for (int v : vs)
         for (int bl : blocks)
@@ -565,7 +566,7 @@ static void release_slot(fqnm_batch* b, int si)
 
 static fqnm_status build_epoch_graph(fqnm_batch* b)
 {
-    BatchKernel kern = batch_kernel(b->plan.v, b->plan.layout);
+    BatchKernel kern = batch_kernel(b->plan.v, b->plan.layout, b->plan.block);
     int per_sm = 0, sms = 0, dev = 0;
     BCK(cudaGetDevice(&dev));
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -630,7 +631,12 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
                             cudaMemcpyDeviceToHost, b->stream));
         BCK(cudaStreamSynchronize(b->stream));
     }
-    for (int si : fresh) {
+    // tables in admission order; when one does not fit, the state blocks of
+    // the later fresh requests are given back first (so that they cannot
+    // starve the earlier one), and the request retries once
+    std::vector<int64_t> requeue;
+    for (size_t f = 0; f < fresh.size(); ++f) {
+        const int si = fresh[f];
         Slot& s = b->slots[si];
         Request& r = b->reqs[s.req];
         if (s.range_pending) {
@@ -641,12 +647,31 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
         bool ok = false;
         fqnm_status st = admit_table(b, si, &ok);
         if (st != FQNM_OK) return st;
-        if (!ok) {                                    // no room for the tables yet
-            const int64_t rid = s.req;
-            r.state = 0;
-            release_slot(b, si);
-            b->queue.push_front(rid);
+        if (!ok) {
+            for (size_t g = f + 1; g < fresh.size(); ++g) {
+                Slot& sg = b->slots[fresh[g]];
+                b->reqs[sg.req].state = 0;
+                requeue.push_back(sg.req);
+                release_slot(b, fresh[g]);
+            }
+            fresh.resize(f + 1);
+            st = admit_table(b, si, &ok);
+            if (st != FQNM_OK) return st;
         }
+        if (!ok) {                                    // no room for the tables yet
+            r.state = 0;
+            requeue.push_back(s.req);
+            release_slot(b, si);
+        }
+    }
+    for (auto it = requeue.rbegin(); it != requeue.rend(); ++it) b->queue.push_front(*it);
+    // nothing on the device and an arrived request still waiting: it cannot
+    // be admitted at all (report it rather than spin)
+    if (b->free_slots.size() == (size_t)b->max_slots) {
+        for (int64_t rid : b->queue)
+            if (b->reqs[rid].arrival_ns <= t)
+                return set_error(FQNM_ERR_OOM, "request %lld cannot be admitted into an empty "
+                                 "batch (budget %zu bytes)", (long long)rid, b->budget);
     }
     // 2. the epoch's launch over every active problem with steps left
     const long long E = (long long)b->plan.block * b->plan.v;
@@ -810,7 +835,7 @@ extern "C" fqnm_status fqnm_batch_progress(fqnm_batch* b, int max_epochs, int* n
 }
 
 extern "C" fqnm_status fqnm_batch_poll(fqnm_batch* b, int64_t id, int32_t* q_out,
-                                       uint64_t* latency_ns, int* done)
+                                       size_t capacity, uint64_t* latency_ns, int* done)
 {
     if (!b || !done) return set_error(FQNM_ERR_ARG, "null argument");
     if (id < 0 || id >= (int64_t)b->reqs.size()) return set_error(FQNM_ERR_ARG, "unknown id %lld", (long long)id);
@@ -818,6 +843,9 @@ extern "C" fqnm_status fqnm_batch_poll(fqnm_batch* b, int64_t id, int32_t* q_out
     *done = 0;
     if (r.state == 3) return set_error(FQNM_ERR_STATE, "result %lld already handed out", (long long)id);
     if (r.state != 2) return FQNM_OK;
+    if (q_out && !r.out_dev && capacity < r.n)
+        return set_error(FQNM_ERR_ARG, "result buffer holds %zu values, problem %lld has %zu",
+                         capacity, (long long)id, r.n);
     if (q_out && !r.out_dev) std::memcpy(q_out, r.result.data(), r.result.size() * sizeof(int32_t));
     if (latency_ns) *latency_ns = r.done_ns - r.arrival_ns;
     *done = 1;

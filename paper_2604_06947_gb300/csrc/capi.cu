@@ -132,7 +132,7 @@ struct fqnm_solver {
     int64_t user_lo = 0;
 
     // options
-    int opt_kernel = 0, opt_layout = 0, opt_v = 0, opt_block = 0, opt_k = 0;
+    int opt_kernel = 0, opt_layout = 0, opt_v = 0, opt_block = 0, opt_k = 0, opt_pdl = -1;
     int64_t margin = 1024;
     int closed_form = 1, recover = 1, autotune = 0, use_graph = 1;
 
@@ -380,8 +380,8 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
         if (value < 0 || value > 2) return set_error(FQNM_ERR_ARG, "layout must be 0..2");
         s->opt_layout = (int)value; break;
     case FQNM_OPT_CELLS_PER_THREAD:
-        if (value != 0 && value != 4 && value != 8 && value != 16)
-            return set_error(FQNM_ERR_ARG, "cells per thread must be 0, 4, 8 or 16");
+        if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
+            return set_error(FQNM_ERR_ARG, "cells per thread must be 0, 4, 8, 16 or 32");
         s->opt_v = (int)value; break;
     case FQNM_OPT_BLOCK:
         if (value != 0 && (value < 32 || value > 512 || value % 32))
@@ -397,6 +397,9 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_RECOVER: s->recover = value != 0; break;
     case FQNM_OPT_AUTOTUNE: s->autotune = value != 0; break;
     case FQNM_OPT_GRAPH: s->use_graph = value != 0; break;
+    case FQNM_OPT_PDL:
+        if (value < 0 || value > 1) return set_error(FQNM_ERR_ARG, "pdl must be 0 or 1");
+        s->opt_pdl = (int)value; break;
     default: return set_error(FQNM_ERR_ARG, "unknown option %d", option);
     }
     if (s->loaded && s->nvars == 1 && option <= FQNM_OPT_K) {
@@ -435,6 +438,7 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
         if (s->tabp) cudaFree(s->tabp);
         s->tab2 = nullptr;
         s->tabp = nullptr;
+        s->tab_cap = 0;
         CK(cudaMalloc(&s->tab2, count * sizeof(int2)));
         CK(cudaMalloc(&s->tabp, count * sizeof(int32_t)));
         s->tab_cap = count;
@@ -527,36 +531,40 @@ static void replan(fqnm_solver* s)
     p.kernel = s->boundary == FQNM_BC_PERIODIC ? 2 : 1;
     if (s->opt_kernel == 1) p.kernel = 1;
     if (s->opt_kernel == 2 && s->boundary == FQNM_BC_PERIODIC) p.kernel = 2;
-    p.layout = table ? LAYOUT_INTERLEAVED : LAYOUT_BLOCKED;
-    if (s->opt_layout) p.layout = s->opt_layout;
+    // default: the plan measured best on table and closed-form maps alike
+    (void)table;
+    p.layout = s->opt_layout ? s->opt_layout : LAYOUT_BLOCKED;
     p.v = s->opt_v ? s->opt_v : 8;
-    p.block = s->opt_block ? s->opt_block : 256;
-    p.k = s->opt_k ? s->opt_k : 32;
+    p.block = s->opt_block ? s->opt_block : 128;
+    p.k = s->opt_k ? s->opt_k : 64;
+    p.pdl = s->opt_pdl < 0 ? 1 : s->opt_pdl;
     const long long E = (long long)p.block * p.v;
     if (2LL * p.k >= E) p.k = (int)std::max(1LL, (E - 1) / 2);
     if (p.kernel == 2 && !tb_plan_supported(s->rule, p)) p.kernel = 1;
     s->plan = p;
 }
 
-// time a few launches of a candidate plan on a scratch buffer
-static float time_plan(fqnm_solver* s, const Plan& p, int reps)
+// Time a candidate plan: `launches` launches that evolve a scratch copy of
+// the current state (ping-pong between two scratch buffers); seconds per step.
+static float time_plan(fqnm_solver* s, const Plan& p, int launches, int32_t* sa, int32_t* sb)
 {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const int32_t* src = (const int32_t*)s->q[s->cur];
-    int32_t* dst = (int32_t*)s->ckpt;          // overwritten below by the caller
-    launch_step_tb(s->rule, p, src, dst, (int64_t)s->n, p.k, s->d_err, s->stream);
+    cudaMemcpyAsync(sa, s->q[s->cur], s->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream);
+    launch_step_tb(s->rule, p, sa, sb, (int64_t)s->n, p.k, s->d_err, s->stream);   // warm-up
     cudaEventRecord(a, s->stream);
-    for (int i = 0; i < reps; ++i)
-        launch_step_tb(s->rule, p, src, dst, (int64_t)s->n, p.k, s->d_err, s->stream);
+    for (int i = 0; i < launches; ++i) {
+        launch_step_tb(s->rule, p, (i & 1) ? sb : sa, (i & 1) ? sa : sb, (int64_t)s->n, p.k,
+                       s->d_err, s->stream);
+    }
     cudaEventRecord(b, s->stream);
     cudaEventSynchronize(b);
     float ms = 0;
     cudaEventElapsedTime(&ms, a, b);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    return ms / (reps * (float)p.k);           // per step
+    return ms / (launches * (float)p.k);           // per step
 }
 
 struct TuneKey {
@@ -582,23 +590,58 @@ static fqnm_status autotune(fqnm_solver* s)
             return FQNM_OK;
         }
     }
-    Plan best = s->plan;
-    float best_t = 1e30f;
+    // stage 1: screen every candidate on a few launches from the loaded
+    // state; stage 2: re-time the six fastest over about 1000 evolving steps
+    int32_t* sb = nullptr;
+    CK(cudaMalloc(&sb, s->n * sizeof(int32_t)));
+    int32_t* sa = (int32_t*)s->ckpt;              // restored by the caller
+    std::vector<std::pair<float, Plan>> screened;
     const int layouts[2] = {LAYOUT_INTERLEAVED, LAYOUT_BLOCKED};
-    const int vs[3] = {4, 8, 16};
-    const int blocks[3] = {128, 256, 512};
-    const int ks[4] = {8, 16, 32, 64};
+    const int vs[4] = {4, 8, 16, 32};
+    const int blocks[5] = {32, 64, 128, 256, 512};
+    const int ks[5] = {8, 16, 32, 64, 128};
     for (int L : layouts)
         for (int v : vs)
             for (int b : blocks)
                 for (int k : ks) {
                     Plan p;
                     p.kernel = 2; p.layout = L; p.v = v; p.block = b; p.k = k;
+                    p.pdl = s->plan.pdl;
                     if (!tb_plan_supported(s->rule, p)) continue;
                     if (4LL * k > (long long)b * v) continue;   // >50% redundant work
-                    const float t = time_plan(s, p, 3);
-                    if (t < best_t) { best_t = t; best = p; }
+                    screened.emplace_back(time_plan(s, p, 3, sa, sb), p);
                 }
+    std::sort(screened.begin(), screened.end(),
+              [](const std::pair<float, Plan>& x, const std::pair<float, Plan>& y) {
+                  return x.first < y.first;
+              });
+    // finalists: the six fastest screened plans and the default plan, each
+    // timed three times (interleaved) over ~2000 evolving steps; the default
+    // stays unless another plan's median is more than 2 % faster
+    const Plan dflt = s->plan;
+    std::vector<Plan> fin;
+    fin.push_back(dflt);
+    for (size_t i = 0; i < screened.size() && fin.size() < 7; ++i) {
+        const Plan& p = screened[i].second;
+        if (p.layout == dflt.layout && p.v == dflt.v && p.block == dflt.block && p.k == dflt.k)
+            continue;
+        fin.push_back(p);
+    }
+    std::vector<std::vector<float>> ts(fin.size());
+    for (int rep = 0; rep < 3; ++rep)
+        for (size_t i = 0; i < fin.size(); ++i)
+            ts[i].push_back(time_plan(s, fin[i], std::max(4, 2048 / fin[i].k), sa, sb));
+    auto median = [](std::vector<float> v) {
+        std::sort(v.begin(), v.end());
+        return v[v.size() / 2];
+    };
+    Plan best = dflt;
+    float best_t = median(ts[0]) / 1.02f;
+    for (size_t i = 1; i < fin.size(); ++i) {
+        const float t = median(ts[i]);
+        if (t < best_t) { best_t = t; best = fin[i]; }
+    }
+    cudaFree(sb);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned), s->stream));
     s->plan = best;
@@ -782,6 +825,7 @@ static bool graph_valid(const fqnm_solver* s)
     const Plan &p = s->plan, &g = s->g_plan;
     return s->gexec && s->g_cur == s->cur && s->g_q0 == s->q[0] && s->g_k == p.k &&
            g.layout == p.layout && g.v == p.v && g.block == p.block && g.kernel == p.kernel &&
+           g.pdl == p.pdl &&
            a.tab2 == b.tab2 && a.tabp == b.tabp && a.lo == b.lo && a.span == b.span &&
            a.evaluator == b.evaluator && a.has_p == b.has_p && a.has_m == b.has_m &&
            a.cf.base == b.cf.base && a.cf.num == b.cf.num && a.cf.den == b.cf.den &&
@@ -1011,6 +1055,14 @@ extern "C" fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
     }
     out->step = s->step_count;
     out->nvars = s->nvars;
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_get_size(fqnm_solver* s, size_t* n_cells, int* nvars)
+{
+    if (!s) return set_error(FQNM_ERR_ARG, "null handle");
+    if (n_cells) *n_cells = s->loaded ? s->n : 0;
+    if (nvars) *nvars = s->nvars;
     return FQNM_OK;
 }
 
@@ -1272,6 +1324,14 @@ static fqnm_status fv_observe(fqnm_fv* f, double* u, bool device)
 
 extern "C" fqnm_status fqnm_fv_observe(fqnm_fv* f, double* u) { return fv_observe(f, u, false); }
 extern "C" fqnm_status fqnm_fv_observe_device(fqnm_fv* f, double* u) { return fv_observe(f, u, true); }
+
+extern "C" fqnm_status fqnm_fv_get_size(fqnm_fv* f, size_t* n_cells, int* nvars)
+{
+    if (!f) return set_error(FQNM_ERR_ARG, "null handle");
+    if (n_cells) *n_cells = f->loaded ? f->n : 0;
+    if (nvars) *nvars = f->nvars;
+    return FQNM_OK;
+}
 
 extern "C" fqnm_status fqnm_fv_launches(fqnm_fv* f, uint64_t* launches)
 {

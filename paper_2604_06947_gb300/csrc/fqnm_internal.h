@@ -56,6 +56,7 @@ struct Plan {
     int v = 8;             // cells per thread
     int block = 256;
     int k = 32;            // steps per launch
+    int pdl = 0;           // launch with programmatic dependent launch
 };
 
 // ---- k_rule.cu --------------------------------------------------------------

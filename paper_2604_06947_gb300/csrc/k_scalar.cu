@@ -42,8 +42,15 @@ __global__ void k_step_naive(RuleView r, const int* __restrict__ qin,
                              int* __restrict__ qout, long long n, int periodic,
                              unsigned* err, long long* bflux)
 {
-    EvTablePM ev{r.tab2, r.lo, r.span};
     unsigned acc = 0;
+    auto ev = [&](int q, int& p, int& m) {             // (phi+, phi-) table gather
+        unsigned k = (unsigned)(q - r.lo);
+        acc = max(acc, k);
+        k = min(k, r.span);
+        const int2 v = r.tab2[k];
+        p = v.x;
+        m = v.y;
+    };
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         long long il = i - 1, ir = i + 1;
@@ -55,9 +62,9 @@ __global__ void k_step_naive(RuleView r, const int* __restrict__ qin,
             if (ir >= n) ir = n - 1;
         }
         int pl, ml, pc, mc, pr, mr;
-        ev(qin[il], pl, ml, acc);
-        ev(qin[i], pc, mc, acc);
-        ev(qin[ir], pr, mr, acc);
+        ev(qin[il], pl, ml);
+        ev(qin[i], pc, mc);
+        ev(qin[ir], pr, mr);
         const int Fr = pc + mr;                    // F_{i+1/2}
         const int Fl = pl + mc;                    // F_{i-1/2}
         qout[i] = qin[i] - (Fr - Fl);
@@ -71,23 +78,38 @@ __global__ void k_step_naive(RuleView r, const int* __restrict__ qin,
 
 // ---- temporal-blocked kernel -----------------------------------------------------
 
-template <class Ev, int V, int LAYOUT>
+template <class Ev, int V, int LAYOUT, bool WARP>
 __global__ void __launch_bounds__(tb::TB_MAX_BLOCK)
 k_step_tb(const int* __restrict__ qin, int* __restrict__ qout, long long n,
           int K, long long S, Ev ev, unsigned* __restrict__ err)
 {
     __shared__ tb::TileSmem sm;
-    tb::tile_step<Ev, V, LAYOUT>(qin, qout, n, K, S, (long long)blockIdx.x, ev, err, sm);
+    tb::tile_step<Ev, V, LAYOUT, WARP>(qin, qout, n, K, S, (long long)blockIdx.x, ev, err, sm);
 }
 
 template <class Ev, int V, int LAYOUT>
-cudaError_t launch_tb_t(const Ev& ev, int block, const int* qin, int* qout,
+cudaError_t launch_tb_t(const Ev& ev, int block, int pdl, const int* qin, int* qout,
                         long long n, int k, unsigned* err, cudaStream_t st)
 {
     const long long E = (long long)block * V;
     const long long S = E - 2LL * k;
     const long long grid = (n + S - 1) / S;
-    k_step_tb<Ev, V, LAYOUT><<<(unsigned)grid, block, 0, st>>>(qin, qout, n, k, S, ev, err);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e;
+    if (block == 32)
+        e = cudaLaunchKernelEx(&cfg, k_step_tb<Ev, V, LAYOUT, true>, qin, qout, n, k, S, ev, err);
+    else
+        e = cudaLaunchKernelEx(&cfg, k_step_tb<Ev, V, LAYOUT, false>, qin, qout, n, k, S, ev, err);
+    if (e != cudaSuccess) return e;
     note_launches();
     return cudaGetLastError();
 }
@@ -99,12 +121,13 @@ cudaError_t dispatch_tb(const Ev& ev, const Plan& p, const int* qin, int* qout,
 #define FQNM_TB_CASE(VV)                                                          \
     if (p.v == VV) {                                                              \
         if (p.layout == LAYOUT_INTERLEAVED)                                       \
-            return launch_tb_t<Ev, VV, LAYOUT_INTERLEAVED>(ev, p.block, qin, qout, n, k, err, st); \
-        return launch_tb_t<Ev, VV, LAYOUT_BLOCKED>(ev, p.block, qin, qout, n, k, err, st); \
+            return launch_tb_t<Ev, VV, LAYOUT_INTERLEAVED>(ev, p.block, p.pdl, qin, qout, n, k, err, st); \
+        return launch_tb_t<Ev, VV, LAYOUT_BLOCKED>(ev, p.block, p.pdl, qin, qout, n, k, err, st); \
     }
     FQNM_TB_CASE(4)
     FQNM_TB_CASE(8)
     FQNM_TB_CASE(16)
+    FQNM_TB_CASE(32)
 #undef FQNM_TB_CASE
     return cudaErrorInvalidValue;
 }
@@ -114,7 +137,7 @@ cudaError_t dispatch_tb(const Ev& ev, const Plan& p, const int* qin, int* qout,
 bool tb_plan_supported(const RuleView& r, const Plan& p)
 {
     (void)r;
-    if (p.v != 4 && p.v != 8 && p.v != 16) return false;
+    if (p.v != 4 && p.v != 8 && p.v != 16 && p.v != 32) return false;
     if (p.block < 32 || p.block > TB_MAX_BLOCK || p.block % 32) return false;
     if (p.layout != LAYOUT_INTERLEAVED && p.layout != LAYOUT_BLOCKED) return false;
     return p.k >= 1 && 2LL * p.k < (long long)p.block * p.v;

@@ -90,24 +90,30 @@ __device__ __forceinline__ long long cell_of(int j)
 constexpr int TB_MAX_BLOCK = 512;
 
 struct TileSmem {
-    int shp[2][TB_MAX_BLOCK / 32];
-    int shm[2][TB_MAX_BLOCK / 32];
+    int shp[2][TB_MAX_BLOCK];
+    int shm[2][TB_MAX_BLOCK];
 };
 
-// All threads of the block must call this with the same arguments.
-template <class Ev, int V, int LAYOUT>
+// All threads of the block must call this with the same arguments.  WARP:
+// the block is one warp (blockDim 32): no shared-memory edge exchange and no
+// block barrier; its two end cells take ghost copies of themselves.
+template <class Ev, int V, int LAYOUT, bool WARP = false>
 __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
                                           int* __restrict__ qout, long long n,
                                           int K, long long S, long long tile,
                                           const Ev& ev, unsigned* __restrict__ err,
                                           TileSmem& sm)
 {
-    int (&shp)[2][TB_MAX_BLOCK / 32] = sm.shp;
-    int (&shm)[2][TB_MAX_BLOCK / 32] = sm.shm;
+    int (&shp)[2][TB_MAX_BLOCK] = sm.shp;
+    int (&shm)[2][TB_MAX_BLOCK] = sm.shm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const long long start = tile * S - K;
 
+    // Programmatic dependent launch: when the previous step launch was
+    // launched as this one's programmatic predecessor, wait here until it has
+    // completed and its stores are visible (a no-op otherwise).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int q[V];
 #pragma unroll
     for (int j = 0; j < V; ++j)
@@ -121,19 +127,24 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
 
         // edge values of each warp for its neighbours: p of the last cell,
         // m of the first cell (double-buffered: one barrier per step)
-        const int b = s & 1;
-        if (lane == 31) shp[b][w] = p[V - 1];
-        if (Ev::HAS_M && lane == 0) shm[b][w] = m[0];
-        __syncthreads();
-        const int pe = shp[b][w > 0 ? w - 1 : 0];            // block edge: invalid anyway
-        const int me = Ev::HAS_M ? shm[b][w < nw - 1 ? w + 1 : w] : 0;
+        // (every lane stores its own value, so no lane-dependent branch; the
+        // reads below pick lane 31 of the previous warp and lane 0 of the next)
+        int pe = 0, me = 0;
+        if (!WARP) {
+            const int b = s & 1;
+            shp[b][threadIdx.x] = p[V - 1];
+            if (Ev::HAS_M) shm[b][threadIdx.x] = m[0];
+            __syncthreads();
+            pe = shp[b][w > 0 ? w * 32 - 1 : 0];              // block edge: invalid anyway
+            me = Ev::HAS_M ? shm[b][w < nw - 1 ? (w + 1) * 32 : 0] : 0;
+        }
 
         // The block's two end cells have no neighbour in the block; they
         // use a ghost copy of themselves (a transmissive end).  Their values
         // are outside the exact region anyway, but this keeps them on a valid
         // scheme, so they stay in the range the maps are verified on.
-        const bool first_owner = (w == 0 && lane == 0);
-        const bool last_owner = (w == nw - 1 && lane == 31);
+        const bool first_owner = WARP ? lane == 0 : (w == 0 && lane == 0);
+        const bool last_owner = WARP ? lane == 31 : (w == nw - 1 && lane == 31);
         if (LAYOUT == LAYOUT_INTERLEAVED) {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
@@ -171,6 +182,9 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
             }
         }
     }
+
+    // let the next step launch start its blocks (they wait for this grid)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     // cells [K, K+S) of the block are exact after K steps
 #pragma unroll

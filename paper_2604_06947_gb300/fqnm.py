@@ -28,7 +28,8 @@ FLUX = {"linear_upwind": 0, "linear_lf": 1, "burgers_lf": 2, "burgers_eo": 3,
 ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
 BOUNDARY = {"periodic": 0, "transmissive": 1}
 OPTION = {"kernel": 0, "layout": 1, "cells_per_thread": 2, "block": 3, "k": 4,
-          "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9}
+          "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9,
+          "pdl": 10}
 
 
 class FqnmError(RuntimeError):
@@ -95,6 +96,7 @@ PROTOTYPES = {
     "fqnm_invariants": (_st, [_vp, _vp, C.POINTER(fqnm_invariants_t)]),
     "fqnm_invariants_noalloc": (_st, [_vp, _vp, C.c_size_t, C.c_int,
                                       C.POINTER(C.c_int64), _vp]),
+    "fqnm_get_size": (_st, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "fqnm_get_rule": (_st, [_vp, C.POINTER(fqnm_rule_info)]),
     "fqnm_get_tables": (_st, [_vp, _vp, _vp]),
     "fqnm_get_stats": (_st, [_vp, C.POINTER(fqnm_stats), C.c_int]),
@@ -108,6 +110,7 @@ PROTOTYPES = {
     "fqnm_fv_observe": (_st, [_vp, _vp]),
     "fqnm_fv_observe_device": (_st, [_vp, _vp]),
     "fqnm_fv_launches": (_st, [_vp, C.POINTER(C.c_uint64)]),
+    "fqnm_fv_get_size": (_st, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "fqnm_batch_create": (_st, [C.c_size_t, C.c_int, _vp, C.POINTER(_vp)]),
     "fqnm_batch_destroy": (_st, [_vp]),
     "fqnm_batch_set_plan": (_st, [_vp, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -116,7 +119,8 @@ PROTOTYPES = {
     "fqnm_batch_submit": (_st, [_vp, C.POINTER(fqnm_problem_spec), _vp, C.c_size_t,
                                 C.c_uint64, C.c_uint64, C.POINTER(C.c_int64)]),
     "fqnm_batch_progress": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
-    "fqnm_batch_poll": (_st, [_vp, C.c_int64, _vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
+    "fqnm_batch_poll": (_st, [_vp, C.c_int64, _vp, C.c_size_t, C.POINTER(C.c_uint64),
+                              C.POINTER(C.c_int)]),
     "fqnm_batch_completed": (_st, [_vp, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int)]),
     "fqnm_batch_submit_device": (_st, [_vp, C.POINTER(fqnm_problem_spec), _vp, C.c_size_t,
                                        C.c_uint64, C.c_uint64, _vp, C.POINTER(C.c_int64)]),
@@ -237,11 +241,15 @@ def fqnm_quantise_device(u_dev, n: int, delta: float, q_dev, rounding: str = "ha
                                        state_bits, _dptr(q_dev), _stream(stream)))
 
 
-def fqnm_load_states(h: int, q, nvars: int = 1):
+def fqnm_load_states(h: int, q, nvars: Optional[int] = None):
+    hv = fqnm_get_size(h)[1]
+    if nvars is not None and nvars != hv:
+        raise ValueError("the solver has %d variables" % hv)
+    nvars = hv
     q = np.ascontiguousarray(q, dtype=np.int32 if nvars == 1 else np.int64)
     n = q.shape[-1] if q.ndim > 1 else q.shape[0]
-    if nvars == 3 and q.size != 3 * n:
-        raise ValueError("Euler states must be [3][n]")
+    if q.size != nvars * n:
+        raise ValueError("states must be [%d][n]" % nvars)
     _check(load().fqnm_load_states(h, q.ctypes.data, n))
 
 
@@ -255,6 +263,9 @@ def fqnm_load_field(h: int, u, n_cells: Optional[int] = None, on_device: bool = 
         _check(load().fqnm_load_field(h, _dptr(u), n_cells, 1))
         return
     u = np.ascontiguousarray(u, dtype=np.float64)
+    nvars = fqnm_get_size(h)[1]
+    if u.size != nvars * u.shape[-1]:
+        raise ValueError("field must be [%d][n] doubles" % nvars)
     _check(load().fqnm_load_field(h, u.ctypes.data, u.shape[-1], 0))
 
 
@@ -266,7 +277,27 @@ def fqnm_sync(h: int):
     _check(load().fqnm_sync(h))
 
 
-def fqnm_observe(h: int, n: int, nvars: int = 1) -> np.ndarray:
+def fqnm_get_size(h: int):
+    """(cells, conserved variables) of the loaded state."""
+    n, nv = C.c_size_t(0), C.c_int(0)
+    _check(load().fqnm_get_size(h, C.byref(n), C.byref(nv)))
+    return n.value, nv.value
+
+
+def _host_size(h: int, n: Optional[int], nvars: Optional[int]):
+    """The handle's own size; a caller's n / nvars must agree with it (the
+    library writes that many values into the host buffer)."""
+    hn, hv = fqnm_get_size(h)
+    if hn == 0:
+        raise FqnmError(-8, "no state loaded")
+    if (n is not None and n != hn) or (nvars is not None and nvars != hv):
+        raise ValueError("size (%s, %s) does not match the loaded state (%d, %d)"
+                         % (n, nvars, hn, hv))
+    return hn, hv
+
+
+def fqnm_observe(h: int, n: Optional[int] = None, nvars: Optional[int] = None) -> np.ndarray:
+    n, nvars = _host_size(h, n, nvars)
     u = np.empty(n * nvars, dtype=np.float64)
     _check(load().fqnm_observe(h, u.ctypes.data))
     return u.reshape(nvars, n) if nvars > 1 else u
@@ -276,7 +307,8 @@ def fqnm_observe_device(h: int, u_dev, fp32: bool = False):
     _check(load().fqnm_observe_device(h, _dptr(u_dev), 1 if fp32 else 0))
 
 
-def fqnm_checkpoint(h: int, n: int, nvars: int = 1):
+def fqnm_checkpoint(h: int, n: Optional[int] = None, nvars: Optional[int] = None):
+    n, nvars = _host_size(h, n, nvars)
     q = np.empty(n * nvars, dtype=np.int32 if nvars == 1 else np.int64)
     step = C.c_uint64(0)
     _check(load().fqnm_checkpoint(h, q.ctypes.data, C.byref(step)))
@@ -349,6 +381,9 @@ def fqnm_fv_set_stream(h: int, stream=None):
 def fqnm_fv_load(h: int, u):
     u = np.ascontiguousarray(u, dtype=np.float64)
     n = u.shape[-1]
+    nvars = fqnm_fv_get_size(h)[1]
+    if u.size != nvars * n:
+        raise ValueError("field must be [%d][n] doubles" % nvars)
     _check(load().fqnm_fv_load(h, u.ctypes.data, n))
 
 
@@ -360,7 +395,20 @@ def fqnm_fv_step(h: int, k: int):
     _check(load().fqnm_fv_step(h, k))
 
 
-def fqnm_fv_observe(h: int, n: int, nvars: int = 1) -> np.ndarray:
+def fqnm_fv_get_size(h: int):
+    n, nv = C.c_size_t(0), C.c_int(0)
+    _check(load().fqnm_fv_get_size(h, C.byref(n), C.byref(nv)))
+    return n.value, nv.value
+
+
+def fqnm_fv_observe(h: int, n: Optional[int] = None, nvars: Optional[int] = None) -> np.ndarray:
+    hn, hv = fqnm_fv_get_size(h)
+    if hn == 0:
+        raise FqnmError(-8, "no field loaded")
+    if (n is not None and n != hn) or (nvars is not None and nvars != hv):
+        raise ValueError("size (%s, %s) does not match the loaded field (%d, %d)"
+                         % (n, nvars, hn, hv))
+    n, nvars = hn, hv
     u = np.empty(n * nvars, dtype=np.float64)
     _check(load().fqnm_fv_observe(h, u.ctypes.data))
     return u.reshape(nvars, n) if nvars > 1 else u
@@ -438,7 +486,7 @@ def fqnm_batch_poll(b: int, rid: int, n: int):
     """(state or None, latency_ns) -- the state is released on success."""
     q = np.empty(n, dtype=np.int32)
     lat, done = C.c_uint64(0), C.c_int(0)
-    _check(load().fqnm_batch_poll(b, rid, q.ctypes.data, C.byref(lat), C.byref(done)))
+    _check(load().fqnm_batch_poll(b, rid, q.ctypes.data, n, C.byref(lat), C.byref(done)))
     return (q, lat.value) if done.value else (None, 0)
 
 
@@ -505,15 +553,21 @@ class Solver:
         fqnm_load_states_device(self.h, q_dev, n)
         return self
 
+    def load_field(self, u, n=None, on_device=False):
+        """Quantise a double field (host array, or device pointer with n)."""
+        fqnm_load_field(self.h, u, n, on_device)
+        self.n = fqnm_get_size(self.h)[0]
+        return self
+
     def step(self, k: int):
         fqnm_step(self.h, k)
         return self
 
     def state(self):
-        return fqnm_checkpoint(self.h, self.n, self.nvars)[0]
+        return fqnm_checkpoint(self.h)[0]
 
     def observe(self):
-        return fqnm_observe(self.h, self.n, self.nvars)
+        return fqnm_observe(self.h)
 
     def invariants(self, other: Optional["Solver"] = None):
         return fqnm_invariants(self.h, other.h if other else None)

@@ -68,7 +68,8 @@ def _percentiles(lat_ns: np.ndarray) -> Dict[str, float]:
 def serve_batched(requests: List[I.ServeRequest], q0s=None,
                   budget_bytes: int = 16 << 30, max_slots: int = 1024,
                   plan: Optional[dict] = None, keep: Optional[set] = None,
-                  lead_s: float = 0.02, dev: Optional[DeviceStream] = None) -> dict:
+                  lead_s: float = 0.02, dev: Optional[DeviceStream] = None,
+                  deadline_s: float = 600.0) -> dict:
     """Run the stream through one batch in real time.
 
     q0s: host initial states (host submission), or dev: a DeviceStream whose
@@ -88,8 +89,12 @@ def serve_batched(requests: List[I.ServeRequest], q0s=None,
         id2req: Dict[int, int] = {}
         t0 = F.fqnm_clock_ns() + int(lead_s * 1e9)
         nxt, done, t_last = 0, 0, t0
+        t_stop = t0 + int(deadline_s * 1e9)
         while done < len(requests):
             now = F.fqnm_clock_ns()
+            if now > t_stop:
+                raise TimeoutError("serving did not finish within %.0f s (%d of %d done)"
+                                   % (deadline_s, done, len(requests)))
             while nxt < len(order):
                 i = order[nxt]
                 t_arr = t0 + int(requests[i].arrival_s * 1e9)

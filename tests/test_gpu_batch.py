@@ -18,8 +18,9 @@ def small_stream(n_requests=48, seed=7, n_max=1 << 14, steps_max=800):
 def test_batched_results_equal_single_and_oracle(orc):
     reqs = small_stream()
     q0s = S.prepare(reqs)
-    # 6 slots and a 3 MiB budget: requests wait for slots and memory
-    bat = S.serve_batched(reqs, q0s, budget_bytes=3 << 20, max_slots=6)
+    # 6 slots and an 8 MiB budget (a Burgers problem needs about 3.1 MB):
+    # requests wait for slots and memory
+    bat = S.serve_batched(reqs, q0s, budget_bytes=8 << 20, max_slots=6, deadline_s=120)
     one = S.serve_one_by_one(reqs, q0s)
     for i in range(len(reqs)):
         assert np.array_equal(bat["results"][i], one["results"][i]), i
@@ -93,6 +94,18 @@ def test_large_problems_in_the_mix(orc):
     one = S.serve_one_by_one(reqs, q0s)
     for i in range(len(reqs)):
         assert np.array_equal(bat["results"][i], one["results"][i])
+
+
+def test_tight_budget_admits_one_at_a_time():
+    """A budget that holds one problem's tables at a time (and the states of
+    several): admission must still make progress, in order."""
+    reqs = small_stream(n_requests=10, seed=21)
+    q0s = S.prepare(reqs)
+    ref = S.serve_one_by_one(reqs, q0s)
+    for budget in (3_300_000, 5 << 20):
+        bat = S.serve_batched(reqs, q0s, budget_bytes=budget, max_slots=6, deadline_s=60)
+        for i in range(len(reqs)):
+            assert np.array_equal(bat["results"][i], ref["results"][i])
 
 
 def test_batch_rejections_are_statuses():

@@ -129,7 +129,10 @@ PLANS = [dict(kernel=1)] + [
     dict(kernel=2, layout=L, cells_per_thread=v, block=b, k=k)
     for L in (1, 2) for v in (4, 8, 16) for b in (64, 256) for k in (1, 7, 32)
 ] + [dict(kernel=2, layout=1, cells_per_thread=8, block=512, k=64),
-     dict(kernel=2, layout=2, cells_per_thread=16, block=512, k=64)]
+     dict(kernel=2, layout=2, cells_per_thread=16, block=512, k=64)] + [
+    dict(kernel=2, layout=L, cells_per_thread=v, block=32, k=k)     # one warp per block
+    for L in (1, 2) for v in (4, 8, 16) for k in (1, 7, 32)
+]
 
 
 @pytest.mark.parametrize("plan", PLANS, ids=lambda d: "-".join("%s%s" % kv for kv in d.items()))
