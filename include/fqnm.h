@@ -131,9 +131,12 @@ typedef enum {
     FQNM_OPT_RECOVER = 7,    /* 1 (default): on range escape widen the map and replay */
     FQNM_OPT_AUTOTUNE = 8,   /* 1: time candidate plans at load and keep the fastest */
     FQNM_OPT_GRAPH = 9,      /* 1 (default): replay long step loops from a CUDA graph */
-    FQNM_OPT_PDL = 10        /* 1 (default): chain step launches with programmatic dependent
+    FQNM_OPT_PDL = 10,       /* 1 (default): chain step launches with programmatic dependent
                                 launch (the next launch's blocks start while the previous
                                 drains, and wait for its results before reading them) */
+    FQNM_OPT_PACK16 = 11     /* 1: when |phi+-| < 2^15 on the range, gather both maps from one
+                                32-bit word (half the table footprint, two more instructions
+                                per cell; 0, the default, is faster while the table fits L1/L2) */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 

@@ -45,6 +45,7 @@ struct BatchDesc {             // one active problem as the batched kernel sees 
     unsigned span;
     const int2* tab2;
     const int* tabp;
+    const int* tab16;          // packed (phi+, phi-) int16 pairs, or null
     unsigned* err;
     ClosedForm cf;
 };
@@ -77,6 +78,9 @@ k_batch_step(const BatchDesc* __restrict__ d, const long long* __restrict__ pref
         } else if (!D.has_m) {
             tb::EvTableP ev{D.tabp, D.lo, D.span};
             tb::tile_step<tb::EvTableP, V, LAYOUT, WARP>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
+        } else if (D.tab16) {
+            tb::EvTablePM16 ev{D.tab16, D.lo, D.span};
+            tb::tile_step<tb::EvTablePM16, V, LAYOUT, WARP>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
         } else {
             tb::EvTablePM ev{D.tab2, D.lo, D.span};
             tb::tile_step<tb::EvTablePM, V, LAYOUT, WARP>(D.qin, D.qout, D.n, D.k, D.S, tile, ev, D.err, sm);
@@ -146,6 +150,8 @@ struct Slot {
     int32_t* q[2] = {nullptr, nullptr};
     int2* tab2 = nullptr;
     int32_t* tabp = nullptr;
+    int32_t* tab16 = nullptr;
+    bool use16 = false;
     int cur = 0;
     uint64_t done = 0;
     int32_t lo = 0;
@@ -203,6 +209,7 @@ struct fqnm_batch {
     int tune_epoch = 0, tune_per_plan = 3;
     // counters
     uint64_t launches = 0, cell_updates = 0, epochs = 0;
+    bool pack16 = false;                     // packed int16 tables (off: faster on GB300)
 };
 
 static void batch_free_device(fqnm_batch* b)
@@ -394,7 +401,7 @@ extern "C" fqnm_status fqnm_batch_get_plan(fqnm_batch* b, int* cells_per_thread,
 static size_t problem_bytes(size_t n, int64_t count)
 {
     return align_up(n * sizeof(int32_t), 256) * 2 + align_up(count * sizeof(int2), 256) +
-           align_up(count * sizeof(int32_t), 256);
+           2 * align_up(count * sizeof(int32_t), 256);
 }
 
 static fqnm_status validate_spec(const fqnm_problem_spec* spec, size_t n)
@@ -518,13 +525,15 @@ static fqnm_status admit_table(fqnm_batch* b, int si, bool* ok)
         return set_error(FQNM_ERR_OOM, "problem %lld needs %zu bytes, the batch budget is %zu",
                          (long long)s.req, problem_bytes(r.n, count), b->budget);
     const size_t t2 = align_up(count * sizeof(int2), 256);
-    const size_t tb = t2 + align_up(count * sizeof(int32_t), 256);
+    const size_t tp = align_up(count * sizeof(int32_t), 256);
+    const size_t tb = t2 + 2 * tp;
     size_t toff = 0;
     if (!arena_alloc(b, tb, &toff)) return FQNM_OK;
     s.toff = toff;
     s.tbytes = tb;
     s.tab2 = (int2*)(b->arena + toff);
     s.tabp = (int32_t*)(b->arena + toff + t2);
+    s.tab16 = (int32_t*)(b->arena + toff + t2 + tp);
     s.lo = (int32_t)lo;
     s.span = (uint32_t)(count - 1);
     const fqnm_flux& f = r.spec.flux;
@@ -697,6 +706,7 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
         d.lo = s.lo;
         d.span = s.span;
         d.tab2 = s.tab2;
+        d.tab16 = s.use16 ? s.tab16 : nullptr;
         d.tabp = s.tabp;
         d.err = b->d_err + si;
         d.cf = s.cf;
@@ -790,6 +800,10 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
         s.check_pending = false;
         const unsigned long long* c = b->h_check + 4 * si;
         s.has_m = (c[1] & CERT_M_NONZERO) != 0;
+        if (b->pack16 && c[2] <= 32767 && c[3] <= 32767) {   // both maps fit int16
+            BCK(launch_pack_tab16(s.tab2, (int64_t)s.span + 1, s.tab16, b->stream));
+            s.use16 = true;
+        }
         if (s.cf_candidate && c[0] == 0 && !s.has_m) s.evaluator = EVAL_CLOSED_FORM;
     }
     // errors restart that problem alone from its initial state (wider map)

@@ -153,7 +153,9 @@ struct fqnm_solver {
     // transfer rule
     int2* tab2 = nullptr;
     int32_t* tabp = nullptr;
+    int32_t* tab16 = nullptr;
     int64_t tab_cap = 0;
+    int pack16 = 0;                        // option: pack the maps as int16 pairs
     RuleView rule{};
     fqnm_rule_info info{};
 
@@ -340,6 +342,7 @@ extern "C" fqnm_status fqnm_destroy(fqnm_solver* s)
     free_state(s);
     if (s->tab2) cudaFree(s->tab2);
     if (s->tabp) cudaFree(s->tabp);
+    if (s->tab16) cudaFree(s->tab16);
     if (s->d_err) cudaFree(s->d_err);
     if (s->d_acc) cudaFree(s->d_acc);
     if (s->d_check) cudaFree(s->d_check);
@@ -397,6 +400,7 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_RECOVER: s->recover = value != 0; break;
     case FQNM_OPT_AUTOTUNE: s->autotune = value != 0; break;
     case FQNM_OPT_GRAPH: s->use_graph = value != 0; break;
+    case FQNM_OPT_PACK16: s->pack16 = value != 0; break;
     case FQNM_OPT_PDL:
         if (value < 0 || value > 1) return set_error(FQNM_ERR_ARG, "pdl must be 0 or 1");
         s->opt_pdl = (int)value; break;
@@ -436,11 +440,14 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
     if (count > s->tab_cap) {
         if (s->tab2) cudaFree(s->tab2);
         if (s->tabp) cudaFree(s->tabp);
+        if (s->tab16) cudaFree(s->tab16);
         s->tab2 = nullptr;
         s->tabp = nullptr;
+        s->tab16 = nullptr;
         s->tab_cap = 0;
         CK(cudaMalloc(&s->tab2, count * sizeof(int2)));
         CK(cudaMalloc(&s->tabp, count * sizeof(int32_t)));
+        CK(cudaMalloc(&s->tab16, count * sizeof(int32_t)));
         s->tab_cap = count;
     }
     CK(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned), s->stream));
@@ -475,6 +482,12 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
     RuleView r{};
     r.tab2 = s->tab2;
     r.tabp = s->tabp;
+    r.tab16 = nullptr;
+    // both maps fit int16: the packed table halves the gather footprint
+    if (s->pack16 && maxp <= 32767 && maxm <= 32767) {
+        CK(launch_pack_tab16(s->tab2, count, s->tab16, s->stream));
+        r.tab16 = s->tab16;
+    }
     r.lo = (int32_t)lo;
     r.span = (uint32_t)(count - 1);
     r.evaluator = EVAL_TABLE;
@@ -826,7 +839,8 @@ static bool graph_valid(const fqnm_solver* s)
     return s->gexec && s->g_cur == s->cur && s->g_q0 == s->q[0] && s->g_k == p.k &&
            g.layout == p.layout && g.v == p.v && g.block == p.block && g.kernel == p.kernel &&
            g.pdl == p.pdl &&
-           a.tab2 == b.tab2 && a.tabp == b.tabp && a.lo == b.lo && a.span == b.span &&
+           a.tab2 == b.tab2 && a.tabp == b.tabp && a.tab16 == b.tab16 && a.lo == b.lo &&
+           a.span == b.span &&
            a.evaluator == b.evaluator && a.has_p == b.has_p && a.has_m == b.has_m &&
            a.cf.base == b.cf.base && a.cf.num == b.cf.num && a.cf.den == b.cf.den &&
            a.cf.magic == b.cf.magic && a.cf.shift == b.cf.shift && a.cf.c0 == b.cf.c0 &&

@@ -42,6 +42,7 @@ struct ClosedForm {
 struct RuleView {
     const int2* tab2;     // (phi+, phi-) for q = lo .. lo+span
     const int32_t* tabp;  // phi+ only (same range)
+    const int32_t* tab16; // phi+ in the low, phi- in the high 16 bits, when both fit int16
     int32_t lo;
     uint32_t span;        // entries - 1
     int32_t evaluator;    // Evaluator
@@ -65,6 +66,9 @@ cudaError_t launch_build_split_table(int kind, double a, double alpha,
                                      int64_t lo, int64_t count, int2* tab2,
                                      int32_t* tabp, unsigned* err,
                                      cudaStream_t st);
+// tab16[k] = (phi+ & 0xffff) | (phi- << 16); caller checks both fit int16
+cudaError_t launch_pack_tab16(const int2* tab2, int64_t count, int32_t* tab16,
+                              cudaStream_t st);
 cudaError_t launch_copy_user_table(const int32_t* p, const int32_t* m,
                                    int64_t count, int2* tab2, int32_t* tabp,
                                    cudaStream_t st);

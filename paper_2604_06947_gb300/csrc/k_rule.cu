@@ -80,6 +80,15 @@ __global__ void k_build_split_table(int kind, double a, double alpha,
     }
 }
 
+__global__ void k_pack_tab16(const int2* tab2, long long count, int32_t* tab16)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int2 v = tab2[k];
+        tab16[k] = (int32_t)(((unsigned)v.x & 0xffffu) | ((unsigned)v.y << 16));
+    }
+}
+
 __global__ void k_copy_user_table(const int32_t* p, const int32_t* m,
                                   long long count, int2* tab2, int32_t* tabp)
 {
@@ -210,6 +219,14 @@ cudaError_t launch_build_split_table(int kind, double a, double alpha,
 {
     k_build_split_table<<<grid_for(count, 256), 256, 0, st>>>(
         kind, a, alpha, delta, lambda, rounding, lo, count, tab2, tabp, err);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_tab16(const int2* tab2, int64_t count, int32_t* tab16,
+                              cudaStream_t st)
+{
+    k_pack_tab16<<<grid_for(count, 256), 256, 0, st>>>(tab2, count, tab16);
     note_launches();
     return cudaGetLastError();
 }

@@ -166,6 +166,10 @@ cudaError_t launch_step_tb(const RuleView& r, const Plan& p, const int32_t* qin,
         EvTableP ev{r.tabp, r.lo, r.span};
         return dispatch_tb(ev, p, qin, qout, n, k, err, st);
     }
+    if (r.tab16) {
+        tb::EvTablePM16 ev{r.tab16, r.lo, r.span};
+        return dispatch_tb(ev, p, qin, qout, n, k, err, st);
+    }
     EvTablePM ev{r.tab2, r.lo, r.span};
     return dispatch_tb(ev, p, qin, qout, n, k, err, st);
 }

@@ -36,6 +36,23 @@ struct EvTablePM {                    // both maps from the (phi+, phi-) table
     }
 };
 
+struct EvTablePM16 {                  // both maps packed as int16 halves of one word
+    static constexpr bool HAS_M = true;
+    const int* __restrict__ tab;
+    int lo;
+    unsigned span;
+    __device__ __forceinline__ void operator()(int q, int& p, int& m,
+                                               unsigned& acc) const
+    {
+        unsigned i = (unsigned)(q - lo);
+        acc = max(acc, i);
+        i = min(i, span);
+        const int v = __ldg(tab + i);
+        p = (int)(short)(v & 0xffff);   // sign-extend the low half
+        m = v >> 16;                    // arithmetic shift keeps the sign
+    }
+};
+
 struct EvTableP {                     // phi- == 0 on the range: phi+ only
     static constexpr bool HAS_M = false;
     const int* __restrict__ tab;
@@ -90,8 +107,8 @@ __device__ __forceinline__ long long cell_of(int j)
 constexpr int TB_MAX_BLOCK = 512;
 
 struct TileSmem {
-    int shp[2][TB_MAX_BLOCK];
-    int shm[2][TB_MAX_BLOCK];
+    int shp[2][TB_MAX_BLOCK / 32];
+    int shm[2][TB_MAX_BLOCK / 32];
 };
 
 // All threads of the block must call this with the same arguments.  WARP:
@@ -104,8 +121,8 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
                                           const Ev& ev, unsigned* __restrict__ err,
                                           TileSmem& sm)
 {
-    int (&shp)[2][TB_MAX_BLOCK] = sm.shp;
-    int (&shm)[2][TB_MAX_BLOCK] = sm.shm;
+    int (&shp)[2][TB_MAX_BLOCK / 32] = sm.shp;
+    int (&shm)[2][TB_MAX_BLOCK / 32] = sm.shm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const long long start = tile * S - K;
@@ -127,16 +144,18 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
 
         // edge values of each warp for its neighbours: p of the last cell,
         // m of the first cell (double-buffered: one barrier per step)
-        // (every lane stores its own value, so no lane-dependent branch; the
-        // reads below pick lane 31 of the previous warp and lane 0 of the next)
+        // (lane 31's p and lane 0's m are broadcast by a shuffle and every
+        // lane stores the same value: one slot per warp, no lane-dependent
+        // branch, and the shared-memory footprint stays small so the L1 that
+        // serves the table gathers keeps its capacity)
         int pe = 0, me = 0;
         if (!WARP) {
             const int b = s & 1;
-            shp[b][threadIdx.x] = p[V - 1];
-            if (Ev::HAS_M) shm[b][threadIdx.x] = m[0];
+            shp[b][w] = __shfl_sync(FULL, p[V - 1], 31);
+            if (Ev::HAS_M) shm[b][w] = __shfl_sync(FULL, m[0], 0);
             __syncthreads();
-            pe = shp[b][w > 0 ? w * 32 - 1 : 0];              // block edge: invalid anyway
-            me = Ev::HAS_M ? shm[b][w < nw - 1 ? (w + 1) * 32 : 0] : 0;
+            pe = shp[b][w > 0 ? w - 1 : 0];                   // block edge: invalid anyway
+            me = Ev::HAS_M ? shm[b][w < nw - 1 ? w + 1 : w] : 0;
         }
 
         // The block's two end cells have no neighbour in the block; they

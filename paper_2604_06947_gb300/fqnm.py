@@ -29,7 +29,7 @@ ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
 BOUNDARY = {"periodic": 0, "transmissive": 1}
 OPTION = {"kernel": 0, "layout": 1, "cells_per_thread": 2, "block": 3, "k": 4,
           "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9,
-          "pdl": 10}
+          "pdl": 10, "pack16": 11}
 
 
 class FqnmError(RuntimeError):
