@@ -47,6 +47,29 @@ def rank_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_problem(rank: int):
+    """One independent problem per rank (weak scaling): the same workload
+    shape, each rank its own seed; no data-path collective."""
+    return I.burgers_problem(seed=I.BASE_SEED + 1 + rank)
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (a time): the job ends with its
+    slowest rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all ranks processed over the job's time."""
+    return units_per_rank * world / seconds
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -63,6 +86,8 @@ def profiled_traffic(kernel_tag: str, src_digest: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         for line in open(path):
+            if line.lstrip().startswith("#"):
+                continue
             f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
             if f.get("kernel") == kernel_tag and f.get("src_sha") == src_digest:
                 return float(f["dram_bytes_per_launch"])
@@ -147,7 +172,7 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     F.load()
 
-    p = I.burgers_problem(seed=I.BASE_SEED + 1 + rank)      # one problem per rank
+    p = rank_problem(rank)
     n, T = p.n, p.steps
     stream = torch.cuda.Stream()
     u0_dev = torch.from_numpy(p.u0).to(dev)
@@ -204,14 +229,8 @@ def run_gpu(args):
     stats = F.fqnm_get_stats(s.h)
     clk = clocks.stop()
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    updates = n * T * args.steps * world
-    value = updates / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = whole_job_rate(n * T * args.steps, world, total_ms / 1e3)
 
     # dominant kernel: the temporal-blocked step, launched only inside the
     # stepping region; average launch duration from the events around it
@@ -236,7 +255,8 @@ def run_gpu(args):
         t1 = time.perf_counter()
         if i > 0:
             e2e_times.append(t1 - t0)
-    e2e_value = n * T / statistics.median(e2e_times) * world
+    e2e_value = whole_job_rate(n * T, world,
+                               max_over_ranks(statistics.median(e2e_times), world, dev))
 
     result = None
     if rank == 0:
@@ -397,7 +417,96 @@ def other_workloads(F, torch, stream):
                                     for k in range(3)),
         "bound": "fp64 pipe (Roe flux, about 100 FP64 operations per face)",
     }
+    # Sod with the density channel alone quantised (§3.3's prototype)
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive", quantise_mask=1)
+    F.fqnm_set_stream(s.h, stream)
+    with torch.cuda.stream(stream):
+        s.load_field(U0, p.n, on_device=True)
+        t_rho = _timed(stream, torch, lambda: (F.fqnm_load_field(s.h, U0, p.n, on_device=True),
+                                               F.fqnm_step(s.h, p.steps)), 1)
+    inv1 = F.fqnm_invariants(s.h)
+    u1 = s.observe()
+    s.close()
+    out["sod_65k_density_only"] = {
+        "n_cells": p.n, "time_steps": p.steps, "seconds": t_rho,
+        "quantised": "rho (m, E in double with the same Roe flux)",
+        "l1_density_vs_componentwise": float(p.dx * np.abs(u1[0] - u[0]).sum()),
+        "l1_density_vs_fv64": float(p.dx * np.abs(u1[0] - ufv[0]).sum()),
+        "density_balance_exact": inv1["mass"][0] == q0[0] - inv1["boundary_flux"][0],
+    }
+    out["burgers_sine_convergence"] = convergence_sweep(F, torch, stream)
+    out["level_statistics_1m"] = level_statistics(F, torch, stream)
     return out
+
+
+def convergence_sweep(F, torch, stream, kmax: int = 14):
+    """The paper's Burgers data (u0 = 0.5 + sin 2 pi x) to t = 0.3 on
+    N = 2^7 .. 2^kmax cells with delta = dx^(3/2) (delta/dx -> 0), against the
+    Hopf-Lax entropy solution on 16 N candidates per period, both on the GPU.
+    Also times the Hopf-Lax kernel (FP64-bound: 4 FP64 operations and a
+    compare per evaluation) on the largest grid."""
+    import math
+    rows, hl = [], {}
+    for k in range(7, kmax + 1):
+        n = 1 << k
+        p = I.burgers_sine_problem(n=n, delta=2.0 ** -math.ceil(1.5 * k))
+        s = F.Solver.for_problem(p)
+        F.fqnm_set_stream(s.h, stream)
+        u0 = torch.from_numpy(p.u0).cuda()
+        with torch.cuda.stream(stream):
+            t = _timed(stream, torch, lambda: (F.fqnm_load_field(s.h, u0, n, on_device=True),
+                                               F.fqnm_step(s.h, p.steps)), 1)
+        u = s.observe()
+        s.close()
+        x = I.cell_centres(n)
+        y, U = I.sine_candidates(16 * n)
+        dx_, dy, dU = (torch.from_numpy(a).cuda() for a in (x, y, U))
+        du = torch.empty(n, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            th = _timed(stream, torch, lambda: F.fqnm_hopf_lax(dx_, dy, dU, 0.3, nx=n, ny=y.size,
+                                                               u=du, stream=stream), 3)
+        ue = du.cpu().numpy()
+        rows.append({"n_cells": n, "delta": p.delta, "time_steps": p.steps, "seconds": t,
+                     "l1_vs_hopf_lax": float(p.dx * np.abs(u - ue).sum())})
+        hl = {"n_points": n, "n_candidates": int(y.size), "seconds": th,
+              "evaluations_per_s": n * y.size / th}
+    e = np.array([r["l1_vs_hopf_lax"] for r in rows])
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp64_peak = 2.0 * sm * 2.07e9                      # FP64 ops/s: 2 per SM per clock
+    hl["fp64_ops_per_s"] = 5 * hl["evaluations_per_s"]
+    hl["fp64_peak_ops_per_s"] = fp64_peak
+    hl["frac_of_fp64_peak"] = hl["fp64_ops_per_s"] / fp64_peak
+    return {"t_end": 0.3, "delta": "dx^(3/2)", "rows": rows,
+            "rates": [float(r) for r in np.log2(e[:-1] / e[1:])], "hopf_lax": hl}
+
+
+def level_statistics(F, torch, stream):
+    """One level-statistics record (histograms, entropy, row-sum defect,
+    sorted transition matrix) on the Burgers 2^20-cell workload after 300
+    steps, against one plain step."""
+    p = I.burgers_problem()
+    s = F.Solver.for_problem(p)
+    F.fqnm_set_stream(s.h, stream)
+    u0 = torch.from_numpy(p.u0).cuda()
+    s.load_field(u0, p.n, on_device=True)
+    s.step(300)
+    rec = s.level_step()                               # grows the work buffers
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        rec = s.level_step()
+    t_rec = (time.perf_counter() - t0) / reps
+    F.fqnm_sync(s.h)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        F.fqnm_step(s.h, 1)
+        F.fqnm_sync(s.h)
+    t_step = (time.perf_counter() - t0) / reps
+    s.close()
+    return {"n_cells": p.n, "seconds_per_record": t_rec, "seconds_per_plain_step": t_step,
+            "record": {k: rec[k] for k in ("step", "occupied", "S", "n_eff", "rho", "pairs",
+                                           "moved")}}
 
 
 def serving_block(torch):

@@ -134,9 +134,15 @@ typedef enum {
     FQNM_OPT_PDL = 10,       /* 1 (default): chain step launches with programmatic dependent
                                 launch (the next launch's blocks start while the previous
                                 drains, and wait for its results before reading them) */
-    FQNM_OPT_PACK16 = 11     /* 1: when |phi+-| < 2^15 on the range, gather both maps from one
+    FQNM_OPT_PACK16 = 11,    /* 1: when |phi+-| < 2^15 on the range, gather both maps from one
                                 32-bit word (half the table footprint, two more instructions
                                 per cell; 0, the default, is faster while the table fits L1/L2) */
+    FQNM_OPT_QUANTISE_MASK = 12 /* EULER_ROE: components evolved by integer transfer, bits
+                                1 rho, 2 m, 4 E (default 7, componentwise).  1 is the density-
+                                channel prototype of §3.3: m and E evolve in double with the
+                                same Roe flux.  A component outside the mask holds the bits of
+                                its double in the int64 state slot (load, checkpoint); its
+                                invariants are reported as 0.  Set before loading. */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 
@@ -227,6 +233,81 @@ fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
 fqnm_status fqnm_invariants_noalloc(const int32_t* q, const int32_t* other,
                                     size_t n, int boundary, int64_t* out,
                                     void* stream);
+
+/* ---- Level statistics (Supplementary Information, Entropy and Statistical
+ * Structure) ------------------------------------------------------------------
+ * For one step q^n -> q^{n+1} of a scalar solver:
+ *   c_k = #{i : q_i = k}, p_k = c_k / N              eq. pk_definition
+ *   S = -sum_k p_k log p_k (natural log)             eq. discrete_entropy
+ *   N_eff = exp(S)                                   eq. neff
+ *   N_{k'k} = #{i : q_i^n = k, q_i^{n+1} = k'}       level-transition counts
+ *   M_{k'k} = N_{k'k} / c_k^n                        eq. empirical_M
+ *   rho = max_{k'} |sum_k M_{k'k} - 1|               row-sum defect
+ * rho runs over the occupied levels k' of p^{n+1} (the only rows of M that
+ * can be nonzero).  Counts are exact.  Each row sum is an exact sum of its
+ * terms N_{k'k}/c_k^n, each rounded to a multiple of 2^-62 (|error| <=
+ * (nonzero entries in the row) 2^-63; exact for a permutation or a column
+ * sent whole to one level), then rounded to double; S is summed in double
+ * in a fixed order.  All results are reproducible run to run.  Scalar (int32) solvers only: FQNM_ERR_ARG
+ * for an Euler solver. */
+typedef struct {
+    uint64_t step;          /* n */
+    int64_t n_cells;
+    int64_t occupied_prev;  /* #{k : c_k^n > 0} */
+    int64_t occupied;       /* #{k : c_k^{n+1} > 0} */
+    double S_prev;          /* S(p^n) */
+    double S;               /* S(p^{n+1}) */
+    double n_eff;           /* exp(S(p^{n+1})) */
+    double rho;             /* row-sum defect of M^n */
+    int64_t rho_level;      /* the smallest k' attaining rho */
+    int64_t pairs;          /* nonzero entries of N^n */
+    int64_t moved;          /* cells with q_i^{n+1} != q_i^n */
+} fqnm_level_stats_t;
+
+/* Advance the solver by exactly one step (as fqnm_step(s, 1), including
+ * range recovery) and compute the statistics of that transition.  Keeps a
+ * device copy of q^n and the sorted nonzero entries of N^n for
+ * fqnm_level_transitions.  Synchronises the solver's stream.  Device memory
+ * is grown on first use (about 40 bytes per cell plus 24 bytes per level
+ * between min and max of the two states) and released by fqnm_destroy. */
+fqnm_status fqnm_level_step(fqnm_solver* s, fqnm_level_stats_t* out);
+
+/* records times: advance every-1 steps, then fqnm_level_step into out[r]
+ * (host array of `records`).  The entropy production rate of Definition
+ * (discrete entropy production rate) is (S - S_prev) / dt of each record. */
+fqnm_status fqnm_level_series(fqnm_solver* s, uint64_t records, uint64_t every,
+                              fqnm_level_stats_t* out);
+
+/* The nonzero entries of N^n of the last fqnm_level_step, sorted by k then k':
+ * host arrays k, k_next, count of capacity cap.  *pairs receives the number
+ * of entries; FQNM_ERR_ARG if cap is smaller (nothing copied), FQNM_ERR_STATE
+ * if no transition was recorded. */
+fqnm_status fqnm_level_transitions(fqnm_solver* s, int64_t* k, int64_t* k_next,
+                                   int64_t* count, size_t cap, size_t* pairs);
+
+/* Dense level counts c_k of the current state over [*lo, *lo + *len), where
+ * lo and lo + len - 1 are the state's min and max, into the host array
+ * counts of capacity cap (FQNM_ERR_ARG, with *lo and *len set, if smaller).
+ * Synchronises the solver's stream. */
+fqnm_status fqnm_level_histogram(fqnm_solver* s, int64_t* lo, int64_t* counts,
+                                 size_t cap, size_t* len);
+
+/* ---- Hopf-Lax entropy reference of inviscid Burgers (§3.2) ------------------
+ * The dense-grid entropy reference of the Burgers test (Lax-Oleinik formula):
+ *   u_i = (x_i - y_{j*}) / t,  j* = argmin_j  U0y_j + (x_i - y_j)^2 / (2 t)
+ * over the candidates (y_j, U0y_j), U0y_j = int_0^{y_j} u0 (periodic data:
+ * pass the periodic images y_j + m with U0y_j + m * mean(u0)).  Evaluated
+ * as d = x_i - y_j; ((d*d) * inv2t) + U0y_j with inv2t = 1/(2t), each
+ * operation rounded once; ties go to the smallest j; a point whose
+ * candidates are all NaN gets u = NaN and idx = -1.
+ * x[nx], y[ny], U0y[ny] in; u[nx] and idx[nx] (int64, may be NULL) out.
+ * on_device = 1: all arrays are device pointers and the call is
+ * asynchronous on `stream` (NULL: the legacy default stream); 0: host arrays,
+ * copied, and the call synchronises.  FQNM_ERR_ARG for a null array, empty
+ * input or t not positive and finite. */
+fqnm_status fqnm_hopf_lax(const double* x, size_t nx, const double* y,
+                          const double* U0y, size_t ny, double t, double* u,
+                          int64_t* idx, int on_device, void* stream);
 
 /* Number of cells and of conserved variables of the loaded state (0 cells
  * before the first load). */

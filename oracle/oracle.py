@@ -80,6 +80,7 @@ def _declare(L):
     L.orc_roe_flux.restype = None
     L.orc_euler_roe_step.argtypes = [_d, _f64p, _d, _d, _i, _i64p, _l, _l, _i64p]
     L.orc_euler_fv_step_f64.argtypes = [_d, _d, _d, _f64p, _l, _l]
+    L.orc_euler_roe_step_mask.argtypes = [_d, _f64p, _d, _d, _i, _i, _i64p, _f64p, _l, _l, _i64p]
     L.orc_riemann_star.argtypes = [_d] * 7 + [_f64p]
     L.orc_riemann_sample.argtypes = [_d] * 9 + [_f64p, _l, _f64p, _f64p, _f64p]
     L.orc_riemann_right_shock_speed.argtypes = [_d] * 7
@@ -87,7 +88,7 @@ def _declare(L):
     for name in ("orc_quantise", "orc_split_table", "orc_step_split",
                  "orc_step_split_faces", "orc_cone", "orc_step_two_point",
                  "orc_invariants", "orc_fv_step_f64", "orc_fv_step_f32",
-                 "orc_euler_roe_step", "orc_euler_fv_step_f64",
+                 "orc_euler_roe_step", "orc_euler_fv_step_f64", "orc_euler_roe_step_mask",
                  "orc_riemann_star", "orc_riemann_sample"):
         getattr(L, name).restype = C.c_int
 
@@ -217,6 +218,20 @@ def euler_step(q, gamma, delta, dx, dt, steps, rounding="half_even"):
                                     dx, dt, ROUNDING[rounding], q.reshape(-1),
                                     n, steps, bf), "euler_step")
     return q, bf
+
+
+def euler_step_mask(q, uf, mask, gamma, delta, dx, dt, steps, rounding="half_even"):
+    """Quantise only the components in mask (1 rho, 2 m, 4 E); the others
+    evolve in double.  q: (3, n) int64 (unmasked rows ignored), uf: (3, n)
+    float64 (masked rows ignored).  Returns (q, uf, boundary_flux)."""
+    q = np.array(q, dtype=np.int64, copy=True, order="C")
+    uf = np.array(uf, dtype=np.float64, copy=True, order="C")
+    n = q.shape[1]
+    bf = np.zeros(3, dtype=np.int64)
+    _check(lib().orc_euler_roe_step_mask(gamma, np.asarray(delta, dtype=np.float64), dx, dt,
+                                         ROUNDING[rounding], mask, q.reshape(-1),
+                                         uf.reshape(-1), n, steps, bf), "euler_step_mask")
+    return q, uf, bf
 
 
 def euler_fv_step(U, gamma, dx, dt, steps):

@@ -48,7 +48,8 @@ def _digest(files) -> str:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
-    h.update(" ".join(NVCC_FLAGS).encode())
+    # the flags without the include path, which depends on where the repo sits
+    h.update(" ".join(f for f in NVCC_FLAGS if not f.startswith("-I")).encode())
     return h.hexdigest()
 
 
@@ -58,7 +59,7 @@ def source_digest() -> str:
     return _digest(files)
 
 
-STEP_KERNEL_SOURCES = ("k_scalar.cu", "closed_form.cuh", "fqnm_internal.h")
+STEP_KERNEL_SOURCES = ("k_scalar.cu", "tile_step.cuh", "closed_form.cuh", "fqnm_internal.h")
 
 
 def kernel_digest(files=STEP_KERNEL_SOURCES) -> str:

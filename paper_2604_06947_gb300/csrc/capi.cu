@@ -6,6 +6,8 @@
 // validates arguments, owns device memory and streams, and sequences
 // launches.
 #include "fqnm_internal.h"
+#include "levels.h"
+#include "hopf_lax.h"
 
 #include <algorithm>
 #include <chrono>
@@ -135,6 +137,7 @@ struct fqnm_solver {
     int opt_kernel = 0, opt_layout = 0, opt_v = 0, opt_block = 0, opt_k = 0, opt_pdl = -1;
     int64_t margin = 1024;
     int closed_form = 1, recover = 1, autotune = 0, use_graph = 1;
+    int qmask = 7;                          // Euler: components evolved as integers
 
     // streams
     cudaStream_t stream = nullptr;
@@ -179,6 +182,11 @@ struct fqnm_solver {
     Plan g_plan;
     RuleView g_rule{};
     const void* g_q0 = nullptr;
+
+    // level statistics (entropy diagnostics), allocated on first use
+    LevelWork* levels = nullptr;
+    LevelRecord level_last{};
+    bool level_valid = false;
 
     size_t state_bytes() const { return nvars == 3 ? sizeof(int64_t) : sizeof(int32_t); }
 };
@@ -339,6 +347,7 @@ extern "C" fqnm_status fqnm_destroy(fqnm_solver* s)
     if (!s) return FQNM_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
     destroy_graph(s);
+    level_work_destroy(s->levels);
     free_state(s);
     if (s->tab2) cudaFree(s->tab2);
     if (s->tabp) cudaFree(s->tabp);
@@ -401,6 +410,11 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_AUTOTUNE: s->autotune = value != 0; break;
     case FQNM_OPT_GRAPH: s->use_graph = value != 0; break;
     case FQNM_OPT_PACK16: s->pack16 = value != 0; break;
+    case FQNM_OPT_QUANTISE_MASK:
+        if (value < 0 || value > 7) return set_error(FQNM_ERR_ARG, "mask must be 0..7");
+        if (s->nvars != 3) return set_error(FQNM_ERR_ARG, "the mask applies to EULER_ROE");
+        if (s->loaded) return set_error(FQNM_ERR_STATE, "set the mask before loading");
+        s->qmask = (int)value; break;
     case FQNM_OPT_PDL:
         if (value < 0 || value > 1) return set_error(FQNM_ERR_ARG, "pdl must be 0 or 1");
         s->opt_pdl = (int)value; break;
@@ -780,6 +794,11 @@ extern "C" fqnm_status fqnm_load_field(fqnm_solver* s, const double* u, size_t n
     CK(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned), s->stream));
     for (int v = 0; v < s->nvars; ++v) {
         char* dst = (char*)s->ckpt + v * n * s->state_bytes();
+        if (s->nvars == 3 && !((s->qmask >> v) & 1)) {     // kept as double bits
+            CK(cudaMemcpyAsync(dst, src + v * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                               s->stream));
+            continue;
+        }
         CK(launch_quantise(src + v * n, (int64_t)n, 1.0 / s->delta[v], s->flux.rounding,
                            s->nvars == 3 ? 64 : 32, dst, s->d_err, s->stream));
     }
@@ -888,7 +907,8 @@ static fqnm_status step_euler(fqnm_solver* s, uint64_t k)
     for (uint64_t i = 0; i < k; ++i) {
         CK(launch_euler_step((int64_t*)s->q[s->cur], (int64_t*)s->q[1 - s->cur],
                              (int64_t)s->n, s->flux.gamma, s->delta, s->lambda,
-                             s->flux.rounding, s->d_err, s->d_acc + ACC_BFLUX, s->stream));
+                             s->flux.rounding, s->qmask, s->d_err, s->d_acc + ACC_BFLUX,
+                             s->stream));
         s->cur = 1 - s->cur;
         s->launches += 1;
     }
@@ -975,7 +995,7 @@ static fqnm_status observe_to(fqnm_solver* s, void* u, int fp32)
         char* dst = (char*)u + v * s->n * es;
         if (s->nvars == 3)
             CK(launch_observe_i64((const int64_t*)s->q[s->cur] + v * s->n, (int64_t)s->n,
-                                  s->delta[v], dst, fp32, s->stream));
+                                  s->delta[v], dst, fp32, s->stream, !((s->qmask >> v) & 1)));
         else
             CK(launch_observe_i32((const int32_t*)s->q[s->cur], (int64_t)s->n, s->delta[0],
                                   dst, fp32, s->stream));
@@ -1048,6 +1068,7 @@ extern "C" fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
     const int periodic = s->boundary == FQNM_BC_PERIODIC;
     for (int v = 0; v < s->nvars; ++v) {
         if (s->nvars == 3) {
+            if (!((s->qmask >> v) & 1)) continue;     // a floating-point component
             const int64_t* q = (const int64_t*)s->q[s->cur] + v * s->n;
             const int64_t* o = other ? (const int64_t*)other->q[other->cur] + v * s->n : nullptr;
             CK(launch_invariants_i64(q, o, (int64_t)s->n, periodic, s->d_acc + 3 * v, s->stream));
@@ -1069,6 +1090,142 @@ extern "C" fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
     }
     out->step = s->step_count;
     out->nvars = s->nvars;
+    return FQNM_OK;
+}
+
+// ---- level statistics (Supplementary Information, entropy appendix) -------------
+
+static fqnm_status level_check(fqnm_solver* s)
+{
+    if (!s) return set_error(FQNM_ERR_ARG, "null handle");
+    if (s->nvars != 1) return set_error(FQNM_ERR_ARG, "level statistics are defined for scalar states");
+    if (!s->loaded) return set_error(FQNM_ERR_STATE, "not loaded");
+    if (!s->levels) s->levels = level_work_create();
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_level_step(fqnm_solver* s, fqnm_level_stats_t* out)
+{
+    fqnm_status st = level_check(s);
+    if (st != FQNM_OK) return st;
+    if (!out) return set_error(FQNM_ERR_ARG, "null output");
+    static_assert(sizeof(LevelRecord) == sizeof(fqnm_level_stats_t), "record layout");
+    st = sync_and_check(s);
+    if (st != FQNM_OK) return st;
+    const uint64_t n0 = s->step_count;
+    s->level_valid = false;
+    CK(level_snapshot(s->levels, (const int32_t*)s->q[s->cur], (int64_t)s->n, s->stream));
+    st = step_any(s, 1);
+    if (st != FQNM_OK) return st;
+    st = sync_and_check(s);                    // a range escape is recovered here
+    if (st != FQNM_OK) return st;
+    const int32_t* qn = level_snap(s->levels);
+    const int32_t* qn1 = (const int32_t*)s->q[s->cur];
+    int64_t lo0, hi0, lo1, hi1;
+    st = state_range(s, qn, &lo0, &hi0);
+    if (st != FQNM_OK) return st;
+    st = state_range(s, qn1, &lo1, &hi1);
+    if (st != FQNM_OK) return st;
+    const int64_t lo = std::min(lo0, lo1), W = std::max(hi0, hi1) - lo + 1;
+    CK(level_transition(s->levels, qn, qn1, (int64_t)s->n, lo, W, s->stream));
+    unsigned e = 0;
+    CK(level_record(s->levels, &s->level_last, &e, s->stream));
+    if (e) return set_error(FQNM_ERR_RANGE, "a level left [%lld, %lld]", (long long)lo,
+                            (long long)(lo + W - 1));
+    s->level_last.step = n0;
+    s->level_valid = true;
+    std::memcpy(out, &s->level_last, sizeof *out);
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_level_series(fqnm_solver* s, uint64_t records, uint64_t every,
+                                         fqnm_level_stats_t* out)
+{
+    fqnm_status st = level_check(s);
+    if (st != FQNM_OK) return st;
+    if (every == 0) return set_error(FQNM_ERR_ARG, "every must be >= 1");
+    if (records && !out) return set_error(FQNM_ERR_ARG, "null output");
+    for (uint64_t r = 0; r < records; ++r) {
+        if (every > 1) {
+            st = step_any(s, every - 1);
+            if (st != FQNM_OK) return st;
+        }
+        st = fqnm_level_step(s, out + r);
+        if (st != FQNM_OK) return st;
+    }
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_level_transitions(fqnm_solver* s, int64_t* k, int64_t* k_next,
+                                              int64_t* count, size_t cap, size_t* pairs)
+{
+    fqnm_status st = level_check(s);
+    if (st != FQNM_OK) return st;
+    if (!s->level_valid) return set_error(FQNM_ERR_STATE, "no recorded transition (call fqnm_level_step)");
+    const size_t m = (size_t)s->level_last.pairs;
+    if (pairs) *pairs = m;
+    if (cap < m) return set_error(FQNM_ERR_ARG, "capacity %zu below the %zu pairs", cap, m);
+    if (m && (!k || !k_next || !count)) return set_error(FQNM_ERR_ARG, "null output");
+    CK(level_export_pairs(s->levels, (int64_t)m, k, k_next, count, s->stream));
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_level_histogram(fqnm_solver* s, int64_t* lo, int64_t* counts,
+                                            size_t cap, size_t* len)
+{
+    fqnm_status st = level_check(s);
+    if (st != FQNM_OK) return st;
+    st = sync_and_check(s);
+    if (st != FQNM_OK) return st;
+    int64_t l, h;
+    st = state_range(s, s->q[s->cur], &l, &h);
+    if (st != FQNM_OK) return st;
+    const size_t W = (size_t)(h - l + 1);
+    if (lo) *lo = l;
+    if (len) *len = W;
+    if (cap < W) return set_error(FQNM_ERR_ARG, "capacity %zu below the %zu levels", cap, W);
+    if (!counts) return set_error(FQNM_ERR_ARG, "null output");
+    unsigned e = 0;
+    CK(level_histogram(s->levels, (const int32_t*)s->q[s->cur], (int64_t)s->n, l, (int64_t)W,
+                       counts, &e, s->stream));
+    if (e) return set_error(FQNM_ERR_RANGE, "a level left [%lld, %lld]", (long long)l, (long long)h);
+    return FQNM_OK;
+}
+
+// ---- Hopf-Lax entropy reference of Burgers (§3.2) ----------------------------------
+
+extern "C" fqnm_status fqnm_hopf_lax(const double* x, size_t nx, const double* y,
+                                     const double* U0y, size_t ny, double t, double* u,
+                                     int64_t* idx, int on_device, void* stream)
+{
+    if (!x || !y || !U0y || !u) return set_error(FQNM_ERR_ARG, "null array");
+    if (nx == 0 || ny == 0) return set_error(FQNM_ERR_ARG, "empty points or candidates");
+    if (nx > (size_t)INT32_MAX * 4 || ny > (size_t)INT64_MAX / 8)
+        return set_error(FQNM_ERR_ARG, "too many points");
+    if (!(t > 0.0) || !(t < 1e300)) return set_error(FQNM_ERR_ARG, "t must be positive and finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (on_device) {
+        CK(launch_hopf_lax(x, (int64_t)nx, y, U0y, (int64_t)ny, t, u, idx, st));
+        return FQNM_OK;
+    }
+    double* d = nullptr;
+    const size_t doubles = 2 * nx + 2 * ny;
+    CK(cudaMallocAsync((void**)&d, doubles * sizeof(double) + nx * sizeof(int64_t), st));
+    double* dx_ = d;
+    double* dy = d + nx;
+    double* dU = dy + ny;
+    double* du = dU + ny;
+    int64_t* di = (int64_t*)(du + nx);
+    cudaError_t e = cudaMemcpyAsync(dx_, x, nx * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, ny * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dU, U0y, ny * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_hopf_lax(dx_, (int64_t)nx, dy, dU, (int64_t)ny, t, du, di, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, nx * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && idx)
+        e = cudaMemcpyAsync(idx, di, nx * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "fqnm_hopf_lax");
     return FQNM_OK;
 }
 

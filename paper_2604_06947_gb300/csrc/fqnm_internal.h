@@ -111,13 +111,16 @@ cudaError_t launch_invariants_i64(const int64_t* q, const int64_t* other,
                                   cudaStream_t st);
 cudaError_t launch_observe_i32(const int32_t* q, int64_t n, double delta,
                                void* u, int fp32, cudaStream_t st);
+// bits != 0: q holds the bits of doubles (an unquantised Euler component)
 cudaError_t launch_observe_i64(const int64_t* q, int64_t n, double delta,
-                               void* u, int fp32, cudaStream_t st);
+                               void* u, int fp32, cudaStream_t st, int bits = 0);
 
 // ---- k_euler.cu -------------------------------------------------------------
+// mask: components evolved as integers (1 rho, 2 m, 4 E); the others hold
+// the bits of a double and take the floating-point update with the same flux
 cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
                               double gamma, const double* delta,
-                              double lambda, int rounding, unsigned* err,
+                              double lambda, int rounding, int mask, unsigned* err,
                               long long* bflux, cudaStream_t st);
 
 // ---- k_fv.cu ----------------------------------------------------------------

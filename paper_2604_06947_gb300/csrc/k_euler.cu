@@ -20,6 +20,7 @@ struct EulerParams {
     double g, lambda;
     double delta[3], inv_delta[3];
     int rounding;
+    int mask;                   // components evolved as integers (1 rho, 2 m, 4 E)
 };
 
 __device__ __forceinline__ double round_mode(double v, int mode)
@@ -29,20 +30,41 @@ __device__ __forceinline__ double round_mode(double v, int mode)
     return rint(v);
 }
 
-__device__ __forceinline__ void face_transfer(const int64_t* __restrict__ q,
-                                              long long n, long long iL,
-                                              long long iR, const EulerParams& P,
-                                              long long* Phi, unsigned* err)
+// A component in the mask holds an integer state (value delta*q); one outside
+// it holds the bits of its double value.
+__device__ __forceinline__ double comp_value(const int64_t* __restrict__ q, long long n,
+                                             long long i, int k, const EulerParams& P)
 {
-    double UL[3], UR[3], F[3];
+    const long long v = q[k * n + i];
+    return ((P.mask >> k) & 1) ? __dmul_rn(P.delta[k], (double)v) : __longlong_as_double(v);
+}
+
+__device__ __forceinline__ RoeCell<double> load_cell(const int64_t* __restrict__ q, long long n,
+                                                    long long i, const EulerParams& P)
+{
+    return roe_cell<double>(P.g, comp_value(q, n, i, 0, P), comp_value(q, n, i, 1, P),
+                            comp_value(q, n, i, 2, P));
+}
+
+__device__ __forceinline__ RoeCell<double> shfl_cell(const RoeCell<double>& c, int src_delta, bool down)
+{
+    RoeCell<double> r;
+#define FQNM_SH(f) r.f = down ? __shfl_down_sync(0xffffffffu, c.f, src_delta) : __shfl_up_sync(0xffffffffu, c.f, src_delta)
+    FQNM_SH(rho); FQNM_SH(m); FQNM_SH(E); FQNM_SH(u); FQNM_SH(p); FQNM_SH(H); FQNM_SH(s);
+#undef FQNM_SH
+    return r;
+}
+
+// The Roe flux of one face and, for the integer components, its quantised
+// transfer round(F lambda / delta).
+__device__ __forceinline__ void transfer(const RoeCell<double>& L, const RoeCell<double>& R,
+                                         const EulerParams& P, long long* Phi, double* F,
+                                         unsigned* err)
+{
+    roe_flux_cells<double>(P.g, L, R, F);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        UL[k] = __dmul_rn(P.delta[k], (double)q[k * n + iL]);
-        UR[k] = __dmul_rn(P.delta[k], (double)q[k * n + iR]);
-    }
-    roe_flux<double>(P.g, UL, UR, F);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
+        if (!((P.mask >> k) & 1)) { Phi[k] = 0; continue; }
         double r = round_mode(__dmul_rn(__dmul_rn(F[k], P.lambda), P.inv_delta[k]), P.rounding);
         if (!(fabs(r) < 4.0e18)) {                 // also NaN (negative pressure)
             atomicOr(err, ERRBIT_OVERFLOW);
@@ -52,38 +74,64 @@ __device__ __forceinline__ void face_transfer(const int64_t* __restrict__ q,
     }
 }
 
+// Cells per warp: a warp loads 32 consecutive cells, the 30 it owns and one
+// neighbour on each side, so that every lane runs the same instructions
+// (a lane that computed an extra face alone would hold the FP64 pipe for a
+// whole warp-instruction per operation).
+constexpr int EULER_OWN = 30;
+
+// Lane l holds cell c0 - 1 + l (clamped to [0, n-1]: the clamp is the
+// transmissive ghost copy) and forms its quantities once; it evaluates the
+// face to its right with its right neighbour's quantities by shuffle, and
+// lanes 1..30 update their cells with the faces of lanes l-1 and l.
 __global__ void k_euler_step(const int64_t* __restrict__ qin,
                              int64_t* __restrict__ qout, long long n,
                              EulerParams P, unsigned* err, long long* bflux)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const long long c = i < n ? i : n - 1;           // tail lanes mirror the last cell
+    const long long c = warp * EULER_OWN - 1 + lane;
+    const long long j = c < 0 ? 0 : (c >= n ? n - 1 : c);
+    const RoeCell<double> me = load_cell(qin, n, j, P);
+    const RoeCell<double> right = shfl_cell(me, 1, true);   // lane 31: unused face
     long long Fr[3], Fl[3];
-    face_transfer(qin, n, c, c + 1 < n ? c + 1 : n - 1, P, Fr, err);
+    double Dr[3], Dl[3];
+    transfer(me, right, P, Fr, Dr, err);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
-    if (lane == 0) face_transfer(qin, n, c > 0 ? c - 1 : 0, c, P, Fl, err);
-    if (i < n) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) qout[k * n + i] = qin[k * n + i] - (Fr[k] - Fl[k]);
-        if (i == 0)
-            for (int k = 0; k < 3; ++k)
-                atomicAdd((unsigned long long*)(bflux + k), (unsigned long long)(-Fl[k]));
-        if (i == n - 1)
-            for (int k = 0; k < 3; ++k)
-                atomicAdd((unsigned long long*)(bflux + k), (unsigned long long)Fr[k]);
+    for (int k = 0; k < 3; ++k) {
+        Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
+        Dl[k] = __shfl_up_sync(0xffffffffu, Dr[k], 1);
     }
+    if (lane < 1 || lane > EULER_OWN || c >= n) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if ((P.mask >> k) & 1) {
+            qout[k * n + c] = qin[k * n + c] - (Fr[k] - Fl[k]);
+        } else {                                       // floating-point update
+            const double u = __longlong_as_double(qin[k * n + c]);
+            qout[k * n + c] = __double_as_longlong(
+                __dsub_rn(u, __dmul_rn(P.lambda, __dsub_rn(Dr[k], Dl[k]))));
+        }
+    }
+    if (c == 0)
+        for (int k = 0; k < 3; ++k)
+            if ((P.mask >> k) & 1)
+                atomicAdd((unsigned long long*)(bflux + k), (unsigned long long)(-Fl[k]));
+    if (c == n - 1)
+        for (int k = 0; k < 3; ++k)
+            if ((P.mask >> k) & 1)
+                atomicAdd((unsigned long long*)(bflux + k), (unsigned long long)Fr[k]);
 }
 
 }  // namespace
 
 cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
                               double gamma, const double* delta, double lambda,
-                              int rounding, unsigned* err, long long* bflux,
+                              int rounding, int mask, unsigned* err, long long* bflux,
                               cudaStream_t st)
 {
     EulerParams P;
+    P.mask = mask;
     P.g = gamma;
     P.lambda = lambda;
     for (int k = 0; k < 3; ++k) {
@@ -92,7 +140,8 @@ cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
     }
     P.rounding = rounding;
     const int block = 128;
-    const long long grid = (n + block - 1) / block;
+    const long long warps = (n + EULER_OWN - 1) / EULER_OWN;
+    const long long grid = (warps * 32 + block - 1) / block;
     k_euler_step<<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);
     note_launches();
     return cudaGetLastError();

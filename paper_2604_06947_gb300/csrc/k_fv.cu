@@ -69,35 +69,52 @@ __global__ void k_fv_step(FvParams<T> P, const T* __restrict__ uin,
 }
 
 template <typename T>
-__device__ __forceinline__ void euler_face(const T* __restrict__ u, long long n,
-                                           long long iL, long long iR, T g, T* F)
+__device__ __forceinline__ RoeCell<T> fv_cell(const T* __restrict__ u, long long n, long long i, T g)
 {
-    T UL[3], UR[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        UL[k] = u[k * n + iL];
-        UR[k] = u[k * n + iR];
-    }
-    roe_flux<T>(g, UL, UR, F);
+    return roe_cell<T>(g, u[i], u[n + i], u[2 * n + i]);
 }
+
+template <typename T>
+__device__ __forceinline__ RoeCell<T> fv_shfl(const RoeCell<T>& c, bool down)
+{
+    RoeCell<T> r;
+#define FQNM_SH(f) r.f = down ? __shfl_down_sync(0xffffffffu, c.f, 1) : __shfl_up_sync(0xffffffffu, c.f, 1)
+    FQNM_SH(rho); FQNM_SH(m); FQNM_SH(E); FQNM_SH(u); FQNM_SH(p); FQNM_SH(H); FQNM_SH(s);
+#undef FQNM_SH
+    return r;
+}
+
+// Cell quantities formed once per cell and shared with the neighbouring
+// lanes, with the same warp layout as the integer Euler kernel: a warp loads
+// 32 cells (its 30 and one on each side, clamped: the transmissive ghost),
+// every lane evaluates the face to its right, lanes 1..30 update.
+constexpr int EULER_FV_OWN = 30;
 
 template <typename T>
 __global__ void k_euler_fv(T g, T lambda, const T* __restrict__ uin,
                            T* __restrict__ uout, long long n)
 {
     using A = Ar<T>;
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long c = i < n ? i : n - 1;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long c = warp * EULER_FV_OWN - 1 + lane;
+    const long long j = c < 0 ? 0 : (c >= n ? n - 1 : c);
+    const RoeCell<T> me = fv_cell<T>(uin, n, j, g);
+    const RoeCell<T> right = fv_shfl<T>(me, true);
     T Fr[3], Fl[3];
-    euler_face<T>(uin, n, c, c + 1 < n ? c + 1 : n - 1, g, Fr);
+    roe_flux_cells<T>(g, me, right, Fr);
 #pragma unroll
     for (int k = 0; k < 3; ++k) Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
-    if ((threadIdx.x & 31) == 0) euler_face<T>(uin, n, c > 0 ? c - 1 : 0, c, g, Fl);
-    if (i < n) {
+    if (lane < 1 || lane > EULER_FV_OWN || c >= n) return;
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            uout[k * n + i] = A::sub(uin[k * n + i], A::mul(lambda, A::sub(Fr[k], Fl[k])));
-    }
+    for (int k = 0; k < 3; ++k)
+        uout[k * n + c] = A::sub(uin[k * n + c], A::mul(lambda, A::sub(Fr[k], Fl[k])));
+}
+
+static unsigned euler_fv_grid(long long n)
+{
+    const long long warps = (n + EULER_FV_OWN - 1) / EULER_FV_OWN;
+    return (unsigned)((warps * 32 + 127) / 128);
 }
 
 template <typename A, typename B>
@@ -133,8 +150,7 @@ cudaError_t launch_fv_step_f32(int kind, double a, double alpha, double lambda,
 cudaError_t launch_euler_fv_f64(double gamma, double lambda, const double* uin,
                                 double* uout, int64_t n, cudaStream_t st)
 {
-    const long long grid = (n + 127) / 128;
-    k_euler_fv<double><<<(unsigned)grid, 128, 0, st>>>(gamma, lambda, uin, uout, n);
+    k_euler_fv<double><<<euler_fv_grid(n), 128, 0, st>>>(gamma, lambda, uin, uout, n);
     note_launches();
     return cudaGetLastError();
 }
@@ -142,8 +158,7 @@ cudaError_t launch_euler_fv_f64(double gamma, double lambda, const double* uin,
 cudaError_t launch_euler_fv_f32(double gamma, double lambda, const float* uin,
                                 float* uout, int64_t n, cudaStream_t st)
 {
-    const long long grid = (n + 127) / 128;
-    k_euler_fv<float><<<(unsigned)grid, 128, 0, st>>>((float)gamma, (float)lambda,
+    k_euler_fv<float><<<euler_fv_grid(n), 128, 0, st>>>((float)gamma, (float)lambda,
                                                       uin, uout, n);
     note_launches();
     return cudaGetLastError();

@@ -64,11 +64,12 @@ k_invariants(const T* __restrict__ q, const T* __restrict__ other, long long n,
 
 template <typename T>
 __global__ void k_observe(const T* __restrict__ q, long long n, double delta,
-                          void* u, int fp32)
+                          void* u, int fp32, int bits)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double v = __dmul_rn(delta, (double)q[i]);
+        const double v = bits ? __longlong_as_double((long long)q[i])
+                              : __dmul_rn(delta, (double)q[i]);
         if (fp32) static_cast<float*>(u)[i] = (float)v;
         else static_cast<double*>(u)[i] = v;
     }
@@ -97,15 +98,15 @@ cudaError_t launch_invariants_i64(const int64_t* q, const int64_t* other,
 cudaError_t launch_observe_i32(const int32_t* q, int64_t n, double delta,
                                void* u, int fp32, cudaStream_t st)
 {
-    k_observe<int32_t><<<grid_for(n, 256), 256, 0, st>>>(q, n, delta, u, fp32);
+    k_observe<int32_t><<<grid_for(n, 256), 256, 0, st>>>(q, n, delta, u, fp32, 0);
     note_launches();
     return cudaGetLastError();
 }
 
 cudaError_t launch_observe_i64(const int64_t* q, int64_t n, double delta,
-                               void* u, int fp32, cudaStream_t st)
+                               void* u, int fp32, cudaStream_t st, int bits)
 {
-    k_observe<int64_t><<<grid_for(n, 256), 256, 0, st>>>(q, n, delta, u, fp32);
+    k_observe<int64_t><<<grid_for(n, 256), 256, 0, st>>>(q, n, delta, u, fp32, bits);
     note_launches();
     return cudaGetLastError();
 }

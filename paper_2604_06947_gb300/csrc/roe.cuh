@@ -39,18 +39,38 @@ template <> struct Ar<float> {
     static __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
 };
 
+// The quantities of one cell that both of its faces use.
 template <typename T>
-__device__ __forceinline__ void roe_flux(T g, const T* UL, const T* UR, T* F)
+struct RoeCell {
+    T rho, m, E, u, p, H, s;
+};
+
+template <typename T>
+__device__ __forceinline__ RoeCell<T> roe_cell(T g, T rho, T m, T E)
+{
+    using A = Ar<T>;
+    const T gm1 = A::sub(g, T(1)), half = T(0.5);
+    RoeCell<T> c;
+    c.rho = rho;
+    c.m = m;
+    c.E = E;
+    c.u = A::div(m, rho);
+    c.p = A::mul(gm1, A::sub(E, A::mul(half, A::mul(rho, A::mul(c.u, c.u)))));
+    c.H = A::div(A::add(E, c.p), rho);
+    c.s = A::sqrt_(rho);
+    return c;
+}
+
+// The Roe flux between two cells whose quantities are already formed (the
+// same operations, in the same order, as roe_flux below).
+template <typename T>
+__device__ __forceinline__ void roe_flux_cells(T g, const RoeCell<T>& L, const RoeCell<T>& R, T* F)
 {
     using A = Ar<T>;
     const T one = T(1), half = T(0.5), gm1 = A::sub(g, one);
-    const T rhoL = UL[0], mL = UL[1], EL = UL[2];
-    const T rhoR = UR[0], mR = UR[1], ER = UR[2];
-    const T uL = A::div(mL, rhoL), uR = A::div(mR, rhoR);
-    const T pL = A::mul(gm1, A::sub(EL, A::mul(half, A::mul(rhoL, A::mul(uL, uL)))));
-    const T pR = A::mul(gm1, A::sub(ER, A::mul(half, A::mul(rhoR, A::mul(uR, uR)))));
-    const T HL = A::div(A::add(EL, pL), rhoL), HR = A::div(A::add(ER, pR), rhoR);
-    const T sL = A::sqrt_(rhoL), sR = A::sqrt_(rhoR), w = A::add(sL, sR);
+    const T rhoL = L.rho, mL = L.m, EL = L.E, uL = L.u, pL = L.p, HL = L.H, sL = L.s;
+    const T rhoR = R.rho, mR = R.m, ER = R.E, uR = R.u, pR = R.p, HR = R.H, sR = R.s;
+    const T w = A::add(sL, sR);
     const T ut = A::div(A::add(A::mul(sL, uL), A::mul(sR, uR)), w);
     const T Ht = A::div(A::add(A::mul(sL, HL), A::mul(sR, HR)), w);
     const T uu = A::mul(ut, ut);
@@ -75,6 +95,12 @@ __device__ __forceinline__ void roe_flux(T g, const T* UL, const T* UR, T* F)
                               A::mul(la3, r3[k]));
         F[k] = A::sub(A::mul(half, A::add(fL[k], fR[k])), A::mul(half, diss));
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void roe_flux(T g, const T* UL, const T* UR, T* F)
+{
+    roe_flux_cells<T>(g, roe_cell<T>(g, UL[0], UL[1], UL[2]), roe_cell<T>(g, UR[0], UR[1], UR[2]), F);
 }
 
 }  // namespace fqnm

@@ -29,7 +29,7 @@ ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
 BOUNDARY = {"periodic": 0, "transmissive": 1}
 OPTION = {"kernel": 0, "layout": 1, "cells_per_thread": 2, "block": 3, "k": 4,
           "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9,
-          "pdl": 10, "pack16": 11}
+          "pdl": 10, "pack16": 11, "quantise_mask": 12}
 
 
 class FqnmError(RuntimeError):
@@ -61,6 +61,13 @@ class fqnm_stats(C.Structure):
                 ("cell_updates", C.c_uint64), ("kernel", C.c_int32),
                 ("layout", C.c_int32), ("cells_per_thread", C.c_int32),
                 ("block", C.c_int32), ("k", C.c_int32), ("graph", C.c_int32)]
+
+
+class fqnm_level_stats_t(C.Structure):
+    _fields_ = [("step", C.c_uint64), ("n_cells", C.c_int64), ("occupied_prev", C.c_int64),
+                ("occupied", C.c_int64), ("S_prev", C.c_double), ("S", C.c_double),
+                ("n_eff", C.c_double), ("rho", C.c_double), ("rho_level", C.c_int64),
+                ("pairs", C.c_int64), ("moved", C.c_int64)]
 
 
 class fqnm_problem_spec(C.Structure):
@@ -97,6 +104,13 @@ PROTOTYPES = {
     "fqnm_invariants_noalloc": (_st, [_vp, _vp, C.c_size_t, C.c_int,
                                       C.POINTER(C.c_int64), _vp]),
     "fqnm_get_size": (_st, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "fqnm_hopf_lax": (_st, [_vp, C.c_size_t, _vp, _vp, C.c_size_t, C.c_double, _vp, _vp,
+                            C.c_int, _vp]),
+    "fqnm_level_step": (_st, [_vp, C.POINTER(fqnm_level_stats_t)]),
+    "fqnm_level_series": (_st, [_vp, C.c_uint64, C.c_uint64, C.POINTER(fqnm_level_stats_t)]),
+    "fqnm_level_transitions": (_st, [_vp, _vp, _vp, _vp, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "fqnm_level_histogram": (_st, [_vp, C.POINTER(C.c_int64), _vp, C.c_size_t,
+                                   C.POINTER(C.c_size_t)]),
     "fqnm_get_rule": (_st, [_vp, C.POINTER(fqnm_rule_info)]),
     "fqnm_get_tables": (_st, [_vp, _vp, _vp]),
     "fqnm_get_stats": (_st, [_vp, C.POINTER(fqnm_stats), C.c_int]),
@@ -337,6 +351,72 @@ def fqnm_invariants_noalloc(q_dev, n: int, other_dev=None, boundary: str = "peri
     return out[0], out[1], out[2]
 
 
+def fqnm_hopf_lax(x, y, U0y, t: float, nx: Optional[int] = None, ny: Optional[int] = None,
+                  u=None, idx=None, stream=None):
+    """Hopf-Lax entropy solution of Burgers at the points x from candidates
+    (y, U0(y)).  Host numpy arrays: returns (u, idx).  Device pointers (with
+    nx, ny and output pointers u, idx): enqueued on `stream`, returns None."""
+    if nx is not None:
+        _check(load().fqnm_hopf_lax(_dptr(x), nx, _dptr(y), _dptr(U0y), ny, t, _dptr(u),
+                                    _dptr(idx) or None, 1, _stream(stream)))
+        return None
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    U0y = np.ascontiguousarray(U0y, dtype=np.float64)
+    if y.shape != U0y.shape:
+        raise ValueError("y and U0y differ in size")
+    u = np.empty(x.size, dtype=np.float64)
+    idx = np.empty(x.size, dtype=np.int64)
+    _check(load().fqnm_hopf_lax(x.ctypes.data, x.size, y.ctypes.data, U0y.ctypes.data, y.size,
+                                t, u.ctypes.data, idx.ctypes.data, 0, None))
+    return u, idx
+
+
+def _level_dict(r: fqnm_level_stats_t) -> dict:
+    return {f: getattr(r, f) for f, _ in fqnm_level_stats_t._fields_}
+
+
+def fqnm_level_step(h: int) -> dict:
+    """One step and the level statistics of that transition (entropy appendix)."""
+    out = fqnm_level_stats_t()
+    _check(load().fqnm_level_step(h, C.byref(out)))
+    return _level_dict(out)
+
+
+def fqnm_level_series(h: int, records: int, every: int) -> list:
+    out = (fqnm_level_stats_t * max(records, 1))()
+    _check(load().fqnm_level_series(h, records, every, out))
+    return [_level_dict(out[r]) for r in range(records)]
+
+
+def fqnm_level_transitions(h: int):
+    """(k, k_next, count) int64 arrays: the nonzero N_{k'k} of the last
+    recorded transition, sorted by k then k'."""
+    m = C.c_size_t(0)
+    st = load().fqnm_level_transitions(h, None, None, None, 0, C.byref(m))
+    if st != FQNM_OK and m.value == 0:
+        _check(st)
+    k = np.empty(m.value, dtype=np.int64)
+    kn = np.empty(m.value, dtype=np.int64)
+    cnt = np.empty(m.value, dtype=np.int64)
+    _check(load().fqnm_level_transitions(h, k.ctypes.data, kn.ctypes.data, cnt.ctypes.data,
+                                         m.value, C.byref(m)))
+    return k, kn, cnt
+
+
+def fqnm_level_histogram(h: int):
+    """(lo, counts): dense level counts of the current state from its min."""
+    lo = C.c_int64(0)
+    n = C.c_size_t(0)
+    st = load().fqnm_level_histogram(h, C.byref(lo), None, 0, C.byref(n))
+    if st != FQNM_OK and n.value == 0:
+        _check(st)
+    counts = np.empty(n.value, dtype=np.int64)
+    _check(load().fqnm_level_histogram(h, C.byref(lo), counts.ctypes.data, n.value,
+                                       C.byref(n)))
+    return lo.value, counts
+
+
 def fqnm_get_rule(h: int) -> dict:
     out = fqnm_rule_info()
     _check(load().fqnm_get_rule(h, C.byref(out)))
@@ -571,6 +651,18 @@ class Solver:
 
     def invariants(self, other: Optional["Solver"] = None):
         return fqnm_invariants(self.h, other.h if other else None)
+
+    def level_step(self) -> dict:
+        return fqnm_level_step(self.h)
+
+    def level_series(self, records: int, every: int) -> list:
+        return fqnm_level_series(self.h, records, every)
+
+    def level_transitions(self):
+        return fqnm_level_transitions(self.h)
+
+    def level_histogram(self):
+        return fqnm_level_histogram(self.h)
 
     def rule(self):
         return fqnm_get_rule(self.h)

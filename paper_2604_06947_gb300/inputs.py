@@ -150,6 +150,38 @@ def burgers_problem(n: int = 1 << 20, delta: float = 2.0 ** -16,
     return p
 
 
+# The paper's Burgers test (§3.2): u0 = 0.5 + sin(2 pi x), past the shock
+# time 1/(2 pi); a fixed dt that lands on t_end exactly.
+SINE_MEAN, SINE_AMP = 0.5, 1.0
+SINE_ALPHA = SINE_MEAN + SINE_AMP      # max |f'| = max |u0| (the range only shrinks)
+
+
+def burgers_sine_problem(n: int = 128, delta: float = 2.0 ** -16, t_end: float = 0.3,
+                         courant: float = 0.4) -> ScalarProblem:
+    """Inviscid Burgers, LF split with alpha = max|u0| = 1.5, periodic,
+    u0 = 0.5 + sin(2 pi x) at the cell centres, steps = ceil(t_end / dt0)
+    with dt0 = courant dx / alpha, then dt = t_end / steps."""
+    dx = 1.0 / n
+    steps = int(np.ceil(t_end / (courant * dx / SINE_ALPHA)))
+    dt = t_end / steps
+    p = ScalarProblem("burgers_sine", "burgers_lf", n, delta, dx, dt, steps,
+                      alpha=SINE_ALPHA)
+    p.u0 = SINE_MEAN + SINE_AMP * np.sin(2.0 * np.pi * cell_centres(n))
+    return p
+
+
+def sine_candidates(ny: int, images=(-1, 0, 1)):
+    """Candidates (y, U0(y)) of the Hopf-Lax reference for u0 = 0.5 + sin(2 pi x):
+    ny points y_j = j / ny of one period and their periodic images y_j + m,
+    with the primitive U0(y) = 0.5 y + (1 - cos 2 pi y) / (2 pi) (input data:
+    the integral of the initial field)."""
+    base = np.arange(ny, dtype=np.float64) / ny
+    U = SINE_MEAN * base + SINE_AMP * (1.0 - np.cos(2.0 * np.pi * base)) / (2.0 * np.pi)
+    y = np.concatenate([base + m for m in images])
+    U0 = np.concatenate([U + SINE_MEAN * m for m in images])
+    return y, U0
+
+
 def high_frequency_problem(n: int = 1 << 24, delta: float = 2.0 ** -20,
                            courant: float = 0.9, steps: int = 2000,
                            seed: int = BASE_SEED + 2,

@@ -88,6 +88,121 @@ def test_sod_65k_full_run_density_error_and_conservation(orc):
 
 
 # ---------------------------------------------------------------------------
+# partial quantisation: only the masked components evolve as integers (§3.3)
+# ---------------------------------------------------------------------------
+
+def masked_start(orc, p, mask):
+    """Oracle start for a mask: integer rows quantised, the others the double
+    field itself."""
+    q = np.zeros((3, p.n), dtype=np.int64)
+    uf = np.array(p.U0, dtype=np.float64)
+    for k in range(3):
+        if (mask >> k) & 1:
+            q[k] = orc.quantise(p.U0[k], p.delta[k])
+    return q, uf
+
+
+def split_state(st, mask):
+    """GPU state rows: integers for masked components, double bits otherwise."""
+    q = np.where([[(mask >> k) & 1] for k in range(3)], st, 0)
+    uf = st.view(np.float64)
+    return q, uf
+
+
+@pytest.mark.parametrize("mask", [1, 5, 0])
+@pytest.mark.parametrize("n", [1000, 1 << 12])
+def test_sod_masked_quantisation_bit_exact(orc, mask, n):
+    """Density-only (mask 1), density and energy (5) and no quantisation (0):
+    every integer row and every double row equal to the oracle's masked step
+    bit for bit, checked every 300 steps, with exact boundary fluxes of the
+    integer rows."""
+    p = I.sod_problem(n=n)
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive", quantise_mask=mask)
+    s.load_field(np.stack(p.U0))
+    q, uf = masked_start(orc, p, mask)
+    bf_total = np.zeros(3, dtype=np.int64)
+    steps = min(p.steps, 1500)
+    done = 0
+    while done < steps:
+        k = min(300, steps - done)
+        s.step(k)
+        q, uf, bf = orc.euler_step_mask(q, uf, mask, p.gamma, p.delta, p.dx, p.dt, k)
+        bf_total += bf
+        done += k
+        gq, guf = split_state(s.state(), mask)
+        for c in range(3):
+            if (mask >> c) & 1:
+                assert np.array_equal(gq[c], q[c]), (c, done)
+            else:
+                assert np.array_equal(guf[c].view(np.int64), uf[c].view(np.int64)), (c, done)
+    u = s.observe()
+    inv = s.invariants()
+    for c in range(3):
+        if (mask >> c) & 1:
+            assert np.array_equal(u[c], p.delta[c] * q[c].astype(np.float64))
+            assert inv["boundary_flux"][c] == bf_total[c]
+            assert inv["mass"][c] == int(q[c].sum())
+        else:
+            assert np.array_equal(u[c], uf[c])
+            assert inv["mass"][c] == 0
+    s.close()
+
+
+def test_sod_mask_zero_is_the_fp64_scheme(orc):
+    """With nothing quantised the solver is the double Roe finite-volume step
+    (the same flux, the same update order)."""
+    p = I.sod_problem(n=2000)
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive", quantise_mask=0)
+    s.load_field(np.stack(p.U0))
+    s.step(400)
+    want = orc.euler_fv_step(p.U0, G, p.dx, p.dt, 400)
+    assert np.array_equal(s.observe(), want)
+    s.close()
+
+
+def test_density_only_mass_is_exact_over_a_full_run(orc):
+    """Full Sod run at 2^14 cells, density alone quantised: its integer mass
+    changes by exactly the counted boundary transfers, and its density stays
+    close to the componentwise and double solutions."""
+    p = I.sod_problem(n=1 << 14)
+    out = {}
+    for mask in (1, 7):
+        s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                     "transmissive", quantise_mask=mask)
+        s.load_field(np.stack(p.U0))
+        m0 = s.invariants()["mass"][0]
+        s.step(p.steps)
+        inv = s.invariants()
+        assert inv["mass"][0] == m0 - inv["boundary_flux"][0]
+        out[mask] = s.observe()[0]
+        s.close()
+    x = I.cell_centres(p.n)
+    rex, _, _ = orc.riemann_sample(G, I.SOD_LEFT, I.SOD_RIGHT, 0.5, 0.2, x)
+    for mask in (1, 7):
+        assert p.dx * np.abs(out[mask] - rex).sum() < 1e-3
+    assert p.dx * np.abs(out[1] - out[7]).sum() < 1e-8
+
+
+def test_mask_rejections():
+    p = I.sod_problem(n=256)
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive")
+    with pytest.raises(F.FqnmError):
+        F.fqnm_set_option(s.h, "quantise_mask", 8)
+    s.load_field(np.stack(p.U0))
+    with pytest.raises(F.FqnmError):
+        F.fqnm_set_option(s.h, "quantise_mask", 1)        # after loading
+    s.close()
+    q = I.linear_advection_problem()
+    s = F.Solver.for_problem(q)
+    with pytest.raises(F.FqnmError):
+        F.fqnm_set_option(s.h, "quantise_mask", 1)        # scalar solver
+    s.close()
+
+
+# ---------------------------------------------------------------------------
 # floating-point finite-volume baselines
 # ---------------------------------------------------------------------------
 

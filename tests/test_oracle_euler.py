@@ -214,3 +214,56 @@ def test_fv64_mass_drifts_only_by_rounding(orc):
     assert abs(u.sum() - u0.sum()) < 1e-9 * np.abs(u0).sum()
     q = orc.step(q0, "burgers_lf", p.delta, p.dx, p.dt, 500, alpha=p.alpha)
     assert q.sum() == q0.sum()
+
+
+# ---------------------------------------------------------------------------
+# partial quantisation (§3.3: the density channel alone on the integer grid)
+# ---------------------------------------------------------------------------
+
+def _masked_start(orc, p, mask):
+    q = np.zeros((3, p.n), dtype=np.int64)
+    for k in range(3):
+        if (mask >> k) & 1:
+            q[k] = orc.quantise(p.U0[k], p.delta[k])
+    return q, np.array(p.U0, dtype=np.float64)
+
+
+def test_mask_all_is_the_componentwise_step(orc):
+    p = I.sod_problem(n=300)
+    q0, uf0 = _masked_start(orc, p, 7)
+    q, _, bf = orc.euler_step_mask(q0, uf0, 7, p.gamma, p.delta, p.dx, p.dt, 250)
+    qc, bfc = orc.euler_step(q0, p.gamma, p.delta, p.dx, p.dt, 250)
+    assert np.array_equal(q, qc) and np.array_equal(bf, bfc)
+
+
+def test_mask_none_is_the_fp64_roe_scheme(orc):
+    p = I.sod_problem(n=300)
+    q0, uf0 = _masked_start(orc, p, 0)
+    q, uf, bf = orc.euler_step_mask(q0, uf0, 0, p.gamma, p.delta, p.dx, p.dt, 250)
+    assert np.array_equal(uf, orc.euler_fv_step(p.U0, p.gamma, p.dx, p.dt, 250))
+    assert not q.any() and not bf.any()
+
+
+@pytest.mark.parametrize("mask", [1, 2, 4, 5])
+def test_masked_rows_conserve_exactly_and_others_track_fp(orc, mask):
+    """Integer rows: mass changes by exactly the counted boundary transfers.
+    Every row stays within a few quanta (integer) or a tiny relative
+    distance (double) of the all-double scheme over 300 steps."""
+    p = I.sod_problem(n=400)
+    q0, uf0 = _masked_start(orc, p, mask)
+    q, uf, bf = orc.euler_step_mask(q0, uf0, mask, p.gamma, p.delta, p.dx, p.dt, 300)
+    ref = orc.euler_fv_step(p.U0, p.gamma, p.dx, p.dt, 300)
+    for k in range(3):
+        if (mask >> k) & 1:
+            assert int(q[k].sum()) == int(q0[k].sum()) - int(bf[k])
+            assert np.abs(p.delta[k] * q[k] - ref[k]).max() < 1e-6
+        else:
+            assert bf[k] == 0
+            assert np.abs(uf[k] - ref[k]).max() < 1e-6
+
+
+def test_mask_rejected_outside_range(orc):
+    p = I.sod_problem(n=16)
+    q0, uf0 = _masked_start(orc, p, 7)
+    with pytest.raises(Exception):
+        orc.euler_step_mask(q0, uf0, 9, p.gamma, p.delta, p.dx, p.dt, 1)
