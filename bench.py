@@ -80,9 +80,9 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(kernel_tag: str, src_digest: str):
-    """Bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+def profiled_counters(kernel_tag: str, src_digest: str) -> dict:
+    """Per-launch counters from the committed ncu summary (profiles/traffic.txt),
+    if they were taken on the current kernel sources (else {})."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         for line in open(path):
@@ -90,10 +90,16 @@ def profiled_traffic(kernel_tag: str, src_digest: str):
                 continue
             f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
             if f.get("kernel") == kernel_tag and f.get("src_sha") == src_digest:
-                return float(f["dram_bytes_per_launch"])
+                return {k: float(v) for k, v in f.items()
+                        if k in ("dram_bytes_per_launch", "warp_instructions_per_launch")}
     except OSError:
         pass
-    return None
+    return {}
+
+
+def profiled_traffic(kernel_tag: str, src_digest: str):
+    """DRAM bytes per launch from the committed ncu summary, or None."""
+    return profiled_counters(kernel_tag, src_digest).get("dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -239,7 +245,8 @@ def run_gpu(args):
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peak()
     kernel_tag = "k_step_tb:L%d:V%d" % (stats["layout"], stats["cells_per_thread"])
-    traffic = profiled_traffic(kernel_tag, B.kernel_digest())
+    counters = profiled_counters(kernel_tag, B.kernel_digest())
+    traffic = counters.get("dram_bytes_per_launch")
 
     # end to end through the C ABI with host buffers (rank-local)
     u0_host = torch.from_numpy(p.u0).pin_memory()
@@ -284,7 +291,8 @@ def run_gpu(args):
                          "kernel": kernel_tag,
                          "bytes_model": "8 B per cell update (int32 read + write), "
                                         "x cells x steps per launch; effective under "
-                                        "temporal blocking"},
+                                        "temporal blocking",
+                         "issue": issue_roofline(counters, avg_launch_s, clk)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "gpu_launches": launches,
@@ -305,6 +313,22 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def issue_roofline(counters: dict, launch_s: float, clk: dict):
+    """The bound the stepping kernel actually meets: warp instructions per
+    launch (committed ncu count on the same sources) over the live launch
+    time, against 4 warp instructions per SM per cycle at the sampled clock."""
+    wi = counters.get("warp_instructions_per_launch")
+    if not wi or not clk or not clk.get("sm_mhz"):
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = 4.0 * sms * clk["sm_mhz"] * 1e6
+    achieved = wi / launch_s
+    return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_launch": wi,
+            "peak_model": "4 issue slots per SM per cycle x SMs x sampled SM clock"}
 
 
 def fv_baselines(F, p, stream, torch):
@@ -435,8 +459,33 @@ def other_workloads(F, torch, stream):
         "l1_density_vs_fv64": float(p.dx * np.abs(u1[0] - ufv[0]).sum()),
         "density_balance_exact": inv1["mass"][0] == q0[0] - inv1["boundary_flux"][0],
     }
+    out["burgers_2d_4096"] = nd_workload(F, torch, stream, (4096, 4096), 240)
+    out["burgers_3d_256"] = nd_workload(F, torch, stream, (256, 256, 256), 96)
     out["burgers_sine_convergence"] = convergence_sweep(F, torch, stream)
     out["level_statistics_1m"] = level_statistics(F, torch, stream)
+    return out
+
+
+def nd_workload(F, torch, stream, dims, steps):
+    """Burgers on a periodic 2-D or 3-D grid (directional composition):
+    device-timed steps, default plan and (2-D) the one-step kernel."""
+    p = I.burgers_nd_problem(dims, steps=steps)
+    u0 = torch.from_numpy(p.u0).cuda()
+    out = {"dims": list(dims), "n_cells": p.n, "time_steps": steps}
+    plans = [("default", {})] + ([("one_step", {"kernel": 1})] if len(dims) == 2 else [])
+    for name, opt in plans:
+        s = F.Solver.for_problem(p, **opt)
+        s.set_grid(p.dims)
+        F.fqnm_set_stream(s.h, stream)
+        with torch.cuda.stream(stream):
+            s.load_field(u0, p.n, on_device=True)
+            m0 = F.fqnm_invariants(s.h)["mass"][0]
+            t = _timed(stream, torch, lambda: F.fqnm_step(s.h, steps), 3)
+        inv = F.fqnm_invariants(s.h)
+        s.close()
+        out[name] = {"seconds": t, "value": p.n * steps / t, "unit": UNIT,
+                     "effective_GBps": BYTES_PER_UPDATE * p.n * steps / t / 1e9,
+                     "mass_exact": inv["mass"][0] == m0}
     return out
 
 

@@ -137,12 +137,18 @@ typedef enum {
     FQNM_OPT_PACK16 = 11,    /* 1: when |phi+-| < 2^15 on the range, gather both maps from one
                                 32-bit word (half the table footprint, two more instructions
                                 per cell; 0, the default, is faster while the table fits L1/L2) */
-    FQNM_OPT_QUANTISE_MASK = 12 /* EULER_ROE: components evolved by integer transfer, bits
+    FQNM_OPT_QUANTISE_MASK = 12, /* EULER_ROE: components evolved by integer transfer, bits
                                 1 rho, 2 m, 4 E (default 7, componentwise).  1 is the density-
                                 channel prototype of §3.3: m and E evolve in double with the
                                 same Roe flux.  A component outside the mask holds the bits of
                                 its double in the int64 state slot (load, checkpoint); its
                                 invariants are reported as 0.  Set before loading. */
+    FQNM_OPT_ND_TILE = 13    /* 2-D grids: register tile of the K-step kernel, x by y cells:
+                                1 64x64, 2 128x64, 3 64x32 (default), 4 128x32, 5 32x128;
+                                FQNM_OPT_K sets K (default 4, below half the smaller side);
+                                FQNM_OPT_KERNEL = 1 selects one step per launch (warps walking
+                                y).  3-D grids always step once per launch (blocks of rows
+                                walking z). */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 
@@ -292,14 +298,29 @@ fqnm_status fqnm_level_transitions(fqnm_solver* s, int64_t* k, int64_t* k_next,
 fqnm_status fqnm_level_histogram(fqnm_solver* s, int64_t* lo, int64_t* counts,
                                  size_t cap, size_t* len);
 
+/* ---- Cartesian grids (Theorem, Cartesian extension by directional
+ * composition; eqs. nd_transfer_rule, nd_flux_definition) ---------------------
+ * Declare the loaded state a periodic d-dimensional grid (d = 2 or 3;
+ * dims[0] fastest, n = dims[0] * ... * dims[d-1]; d = 1 restores the line).
+ * Each step then applies the solver's one-dimensional rule along every axis:
+ *   q_i <- q_i - sum_m (F_{i+e_m/2} - F_{i-e_m/2}),
+ *   F_{i+e_m/2} = phi+(q_i) + phi-(q_{i+e_m}),
+ * all fluxes from the state before the step.  Mass is conserved exactly;
+ * fqnm_invariants reports TV summed over the axes.  Call before loading, on
+ * a periodic scalar solver.  FQNM_ERR_CFL when d * (Courant number) > 1
+ * (the monotonicity bound of the composed scheme), FQNM_ERR_ARG for a bad
+ * shape, FQNM_ERR_STATE after loading. */
+fqnm_status fqnm_set_grid(fqnm_solver* s, int d, const size_t* dims);
+
 /* ---- Hopf-Lax entropy reference of inviscid Burgers (§3.2) ------------------
  * The dense-grid entropy reference of the Burgers test (Lax-Oleinik formula):
  *   u_i = (x_i - y_{j*}) / t,  j* = argmin_j  U0y_j + (x_i - y_j)^2 / (2 t)
  * over the candidates (y_j, U0y_j), U0y_j = int_0^{y_j} u0 (periodic data:
  * pass the periodic images y_j + m with U0y_j + m * mean(u0)).  Evaluated
  * as d = x_i - y_j; ((d*d) * inv2t) + U0y_j with inv2t = 1/(2t), each
- * operation rounded once; ties go to the smallest j; a point whose
- * candidates are all NaN gets u = NaN and idx = -1.
+ * operation rounded once; ties go to the smallest j (-0 and +0 tie); NaN
+ * objectives are never the minimum, and a point whose objectives are all
+ * NaN or +inf gets u = NaN and idx = -1.
  * x[nx], y[ny], U0y[ny] in; u[nx] and idx[nx] (int64, may be NULL) out.
  * on_device = 1: all arrays are device pointers and the call is
  * asynchronous on `stream` (NULL: the legacy default stream); 0: host arrays,

@@ -72,6 +72,7 @@ def _declare(L):
     L.orc_two_point_phi.restype = C.c_int64
     L.orc_step_two_point.argtypes = [_i, _d, _d, _d, _d, _d, _i, _i, _i64p, _l, _l]
     L.orc_invariants.argtypes = [_i64p, _l, C.c_void_p, _i, _i64p]
+    L.orc_step_nd.argtypes = [_i, _d, _d, _d, _d, _d, _i, _i, _i64p, _i64p, _l]
     L.orc_level_entropy.argtypes = [_i64p, _l]
     L.orc_level_entropy.restype = _d
     L.orc_fv_step_f64.argtypes = [_i, _d, _d, _d, _d, _i, _f64p, _l, _l]
@@ -85,7 +86,7 @@ def _declare(L):
     L.orc_riemann_sample.argtypes = [_d] * 9 + [_f64p, _l, _f64p, _f64p, _f64p]
     L.orc_riemann_right_shock_speed.argtypes = [_d] * 7
     L.orc_riemann_right_shock_speed.restype = _d
-    for name in ("orc_quantise", "orc_split_table", "orc_step_split",
+    for name in ("orc_quantise", "orc_split_table", "orc_step_split", "orc_step_nd",
                  "orc_step_split_faces", "orc_cone", "orc_step_two_point",
                  "orc_invariants", "orc_fv_step_f64", "orc_fv_step_f32",
                  "orc_euler_roe_step", "orc_euler_fv_step_f64", "orc_euler_roe_step_mask",
@@ -127,6 +128,17 @@ def step(q, kind, delta, dx, dt, steps, a=0.0, alpha=0.0,
                                 ROUNDING[rounding], BOUNDARY[boundary], q,
                                 q.shape[0], steps, C.byref(bf)), "step")
     return (q, bf.value) if return_bflux else q
+
+
+def step_nd(q, kind, delta, dx, dt, steps, a=0.0, alpha=0.0, rounding="half_even"):
+    """Advance a copy of the periodic d-dimensional state q (numpy array of
+    shape (nz, ny, nx), (ny, nx) or (nx,); x fastest) by `steps` steps of the
+    directional composition (eq. nd_transfer_rule)."""
+    q = np.array(q, dtype=np.int64, copy=True, order="C")
+    dims = np.array(q.shape[::-1], dtype=np.int64)
+    _check(lib().orc_step_nd(KINDS[kind], a, alpha, delta, dx, dt, ROUNDING[rounding],
+                             q.ndim, dims, q.reshape(-1), steps), "step_nd")
+    return q
 
 
 def step_faces(q, kind, delta, dx, dt, steps, a=0.0, alpha=0.0,

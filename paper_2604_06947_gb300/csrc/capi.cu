@@ -8,6 +8,7 @@
 #include "fqnm_internal.h"
 #include "levels.h"
 #include "hopf_lax.h"
+#include "nd.h"
 
 #include <algorithm>
 #include <chrono>
@@ -138,6 +139,8 @@ struct fqnm_solver {
     int64_t margin = 1024;
     int closed_form = 1, recover = 1, autotune = 0, use_graph = 1;
     int qmask = 7;                          // Euler: components evolved as integers
+    NdGrid grid{1, {0, 1, 1}};              // d > 1: the Cartesian step of Theorem (extension)
+    int opt_nd_tile = 0;                    // 2-D tile shape (0: default)
 
     // streams
     cudaStream_t stream = nullptr;
@@ -410,6 +413,9 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_AUTOTUNE: s->autotune = value != 0; break;
     case FQNM_OPT_GRAPH: s->use_graph = value != 0; break;
     case FQNM_OPT_PACK16: s->pack16 = value != 0; break;
+    case FQNM_OPT_ND_TILE:
+        if (value < 0 || value > ND_TILE_32x128) return set_error(FQNM_ERR_ARG, "tile shape 0..5");
+        s->opt_nd_tile = (int)value; break;
     case FQNM_OPT_QUANTISE_MASK:
         if (value < 0 || value > 7) return set_error(FQNM_ERR_ARG, "mask must be 0..7");
         if (s->nvars != 3) return set_error(FQNM_ERR_ARG, "the mask applies to EULER_ROE");
@@ -607,7 +613,7 @@ static std::map<TuneKey, Plan> g_tune_cache;
 
 static fqnm_status autotune(fqnm_solver* s)
 {
-    if (s->plan.kernel != 2) return FQNM_OK;
+    if (s->plan.kernel != 2 || s->grid.d > 1) return FQNM_OK;
     TuneKey key{(int64_t)bit_length((uint64_t)s->n), s->rule.evaluator, s->rule.has_m};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -731,6 +737,8 @@ static fqnm_status load_common(fqnm_solver* s, const void* q, size_t n, bool dev
     if (!s) return set_error(FQNM_ERR_ARG, "null handle");
     if (!q || n == 0) return set_error(FQNM_ERR_ARG, "null states or n == 0");
     if (n > (size_t)INT32_MAX) return set_error(FQNM_ERR_ARG, "n too large");
+    if (s->grid.d > 1 && (long long)n != s->grid.cells())
+        return set_error(FQNM_ERR_ARG, "%zu states for a grid of %lld cells", n, s->grid.cells());
     fqnm_status st = ensure_runtime(s);
     if (st != FQNM_OK) return st;
     s->loaded = false;
@@ -866,8 +874,41 @@ static bool graph_valid(const fqnm_solver* s)
            a.cf.rounding == b.cf.rounding;
 }
 
+// The 2-D plan: temporal-blocked tiles unless the one-step kernel was asked
+// for (FQNM_OPT_KERNEL = 1) or the grid is 3-D.
+static NdPlan nd_plan(const fqnm_solver* s)
+{
+    NdPlan p;
+    p.blocked = s->grid.d == 2 && s->opt_kernel != 1;
+    if (s->opt_nd_tile) p.shape = s->opt_nd_tile;
+    const int lim = std::min(nd_tile_x(p.shape), nd_tile_y(p.shape)) / 2 - 1;
+    p.k = s->opt_k > 0 ? std::min(s->opt_k, lim) : std::min(4, lim);
+    return p;
+}
+
 static fqnm_status step_scalar(fqnm_solver* s, uint64_t k)
 {
+    if (s->grid.d > 1) {
+        // 2-D: K steps per launch in register tiles (unless the one-step
+        // kernel is asked for); 3-D: one step per launch
+        const NdPlan np = nd_plan(s);
+        uint64_t done = 0;
+        while (done < k) {
+            if (np.blocked) {
+                const int kk = (int)std::min<uint64_t>((uint64_t)np.k, k - done);
+                CK(launch_step2d_tb(s->rule, np, (const int32_t*)s->q[s->cur],
+                                    (int32_t*)s->q[1 - s->cur], s->grid, kk, s->d_err, s->stream));
+                done += kk;
+            } else {
+                CK(launch_step_nd(s->rule, (const int32_t*)s->q[s->cur], (int32_t*)s->q[1 - s->cur],
+                                  s->grid, s->d_err, s->stream));
+                done += 1;
+            }
+            s->cur = 1 - s->cur;
+            s->launches += 1;
+        }
+        return FQNM_OK;
+    }
     if (s->plan.kernel == 1) {
         for (uint64_t i = 0; i < k; ++i) {
             CK(launch_step_naive(s->rule, (int32_t*)s->q[s->cur], (int32_t*)s->q[1 - s->cur],
@@ -1072,6 +1113,10 @@ extern "C" fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
             const int64_t* q = (const int64_t*)s->q[s->cur] + v * s->n;
             const int64_t* o = other ? (const int64_t*)other->q[other->cur] + v * s->n : nullptr;
             CK(launch_invariants_i64(q, o, (int64_t)s->n, periodic, s->d_acc + 3 * v, s->stream));
+        } else if (s->grid.d > 1) {
+            const int32_t* o = other ? (const int32_t*)other->q[other->cur] : nullptr;
+            CK(launch_invariants_nd((const int32_t*)s->q[s->cur], o, s->grid, s->d_acc,
+                                    s->stream));
         } else {
             const int32_t* o = other ? (const int32_t*)other->q[other->cur] : nullptr;
             CK(launch_invariants_i32((const int32_t*)s->q[s->cur], o, (int64_t)s->n, periodic,
@@ -1226,6 +1271,40 @@ extern "C" fqnm_status fqnm_hopf_lax(const double* x, size_t nx, const double* y
     cudaFreeAsync(d, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_error(e, "fqnm_hopf_lax");
+    return FQNM_OK;
+}
+
+// ---- Cartesian grids (Theorem, extension by directional composition) -------------
+
+extern "C" fqnm_status fqnm_set_grid(fqnm_solver* s, int d, const size_t* dims)
+{
+    if (!s) return set_error(FQNM_ERR_ARG, "null handle");
+    if (s->loaded) return set_error(FQNM_ERR_STATE, "set the grid before loading");
+    if (d < 1 || d > 3 || (d > 1 && !dims)) return set_error(FQNM_ERR_ARG, "d must be 1, 2 or 3");
+    if (s->nvars != 1) return set_error(FQNM_ERR_ARG, "grids are for scalar solvers");
+    if (d > 1 && s->boundary != FQNM_BC_PERIODIC)
+        return set_error(FQNM_ERR_ARG, "d > 1 grids are periodic");
+    NdGrid g{d, {1, 1, 1}};
+    long long cells = 1;
+    for (int m = 0; m < d && d > 1; ++m) {
+        if (dims[m] == 0 || dims[m] > (size_t)INT32_MAX)
+            return set_error(FQNM_ERR_ARG, "dims[%d] = %zu", m, dims[m]);
+        g.dims[m] = (long long)dims[m];
+        cells *= g.dims[m];
+        if (cells > (long long)INT32_MAX) return set_error(FQNM_ERR_ARG, "too many cells");
+    }
+    // monotone (Lemma on CFL stability per axis summed): d nu <= 1
+    if (d > 1 && !s->user_table) {
+        double nu = 0;
+        const double lam = s->lambda;
+        if (s->flux.kind == FQNM_FLUX_LINEAR_UPWIND) nu = std::fabs(s->flux.a) * lam;
+        else nu = s->flux.alpha * lam;
+        if (d * nu > 1.0)
+            return set_error(FQNM_ERR_CFL, "d * Courant number = %.17g > 1", d * nu);
+    }
+    if (d == 1) g = NdGrid{1, {0, 1, 1}};
+    s->grid = g;
+    destroy_graph(s);
     return FQNM_OK;
 }
 

@@ -11,8 +11,10 @@
 //
 // A warp holds R rows (x values) in registers and its lanes stride over the
 // candidates, each candidate load serving R evaluations; the warp then
-// reduces each row's (value, index) pairs.  FP64-bound: 4 FP64 operations
-// and one FP64 compare per evaluation.
+// reduces each row's (value, index) pairs.  FP64-bound: the 4 FP64
+// operations of an evaluation run on the FP64 pipe (2 per SM per cycle on
+// this part); the comparison runs on the integer pipe, on keys that order
+// as the doubles do (-0 folded onto +0, NaN above every number).
 #include "fqnm_internal.h"
 #include "hopf_lax.h"
 
@@ -24,6 +26,18 @@ namespace {
 
 constexpr int HL_ROWS = 4;
 constexpr int HL_THREADS = 256;
+constexpr long long KEY_INF = 0x7ff0000000000000LL;     // key of +inf (and its bits)
+constexpr long long KEY_NAN = 0x7fffffffffffffffLL;     // above every number
+
+// An int64 that orders as the double does: a < b <=> key(a) < key(b) and
+// a == b <=> key(a) == key(b) for non-NaN a, b.
+__device__ __forceinline__ long long order_key(double v)
+{
+    long long b = __double_as_longlong(v);
+    if ((b & KEY_NAN) > KEY_INF) return KEY_NAN;           // NaN
+    if (b == (long long)0x8000000000000000ULL) b = 0;       // -0 -> +0
+    return b >= 0 ? b : b ^ KEY_NAN;
+}
 
 __global__ void __launch_bounds__(HL_THREADS)
 k_hopf_lax(const double* __restrict__ x, long long nx, const double* __restrict__ y,
@@ -34,12 +48,13 @@ k_hopf_lax(const double* __restrict__ x, long long nx, const double* __restrict_
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long r0 = warp * HL_ROWS;
     if (r0 >= nx) return;                               // the whole warp leaves
-    double xr[HL_ROWS], best[HL_ROWS];
+    double xr[HL_ROWS];
+    long long best[HL_ROWS];                            // order keys
     long long bj[HL_ROWS];
 #pragma unroll
     for (int r = 0; r < HL_ROWS; ++r) {
         xr[r] = x[r0 + r < nx ? r0 + r : r0];
-        best[r] = __longlong_as_double(0x7ff0000000000000LL);     // +inf
+        best[r] = KEY_INF;                              // +inf: never taken
         bj[r] = LLONG_MAX;
     }
     for (long long j = lane; j < ny; j += 32) {
@@ -47,7 +62,7 @@ k_hopf_lax(const double* __restrict__ x, long long nx, const double* __restrict_
 #pragma unroll
         for (int r = 0; r < HL_ROWS; ++r) {
             const double d = __dsub_rn(xr[r], yj);
-            const double o = __dadd_rn(Uj, __dmul_rn(__dmul_rn(d, d), inv2t));
+            const long long o = order_key(__dadd_rn(Uj, __dmul_rn(__dmul_rn(d, d), inv2t)));
             if (o < best[r]) {                          // first minimum of this lane
                 best[r] = o;
                 bj[r] = j;
@@ -58,7 +73,7 @@ k_hopf_lax(const double* __restrict__ x, long long nx, const double* __restrict_
     for (int r = 0; r < HL_ROWS; ++r) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            const double ob = __shfl_down_sync(0xffffffffu, best[r], off);
+            const long long ob = __shfl_down_sync(0xffffffffu, best[r], off);
             const long long oj = __shfl_down_sync(0xffffffffu, bj[r], off);
             if (ob < best[r] || (ob == best[r] && oj < bj[r])) {
                 best[r] = ob;

@@ -224,27 +224,27 @@ __global__ void k_level_defect(const unsigned* __restrict__ hist,
     if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
-// One block: combine the partials in a fixed order into the record.
-__global__ void k_level_finish(const double* __restrict__ ps_prev,
-                               const unsigned long long* __restrict__ po_prev,
-                               const double* __restrict__ ps, const unsigned long long* __restrict__ po,
-                               const DefectArg* __restrict__ pd, int parts,
-                               const unsigned* __restrict__ pairs,
-                               const unsigned long long* __restrict__ moved,
-                               long long n, long long lo, LevelRecord* __restrict__ rec)
+// One block of REDUCE_BLOCKS threads: combine the partials (thread j holds
+// partial j) by fixed-order block reductions into the record.
+__global__ void __launch_bounds__(REDUCE_BLOCKS)
+k_level_finish(const double* __restrict__ ps_prev, const unsigned long long* __restrict__ po_prev,
+               const double* __restrict__ ps, const unsigned long long* __restrict__ po,
+               const DefectArg* __restrict__ pd, const unsigned* __restrict__ pairs,
+               const unsigned long long* __restrict__ moved, long long n, long long lo,
+               LevelRecord* __restrict__ rec)
 {
-    if (threadIdx.x != 0) return;
-    double s0 = 0.0, s1 = 0.0;
-    unsigned long long o0 = 0, o1 = 0;
-    DefectArg best{0, 0, NO_ROW};
-    for (int j = 0; j < parts; ++j) {
-        s0 = __dadd_rn(s0, ps_prev[j]);
-        s1 = __dadd_rn(s1, ps[j]);
-        o0 += po_prev[j];
-        o1 += po[j];
-        const DefectArg v = pd[j];
-        if (v.k != NO_ROW && (best.k == NO_ROW || better(v, best))) best = v;
-    }
+    __shared__ double shd[32];
+    __shared__ unsigned long long shu[32];
+    __shared__ DefectArg sha[32];
+    const int j = threadIdx.x;
+    const double s0 = block_sum<double>(ps_prev[j], shd);
+    const double s1 = block_sum<double>(ps[j], shd);
+    const unsigned long long o0 = block_sum<unsigned long long>(po_prev[j], shu);
+    const unsigned long long o1 = block_sum<unsigned long long>(po[j], shu);
+    DefectArg v = pd[j];
+    if (v.k == NO_ROW) { v.dh = 0; v.dl = 0; }
+    const DefectArg best = block_best(v, sha);
+    if (j != 0) return;
     rec->n_cells = n;
     rec->occupied_prev = (long long)o0;
     rec->occupied = (long long)o1;
@@ -645,9 +645,9 @@ cudaError_t level_transition(LevelWork* w, const int32_t* qn, const int32_t* qn1
     k_level_defect<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(w->hist[1], w->acc, w->acc + W, uW,
                                                              w->part_def);
     launches += 4;
-    k_level_finish<<<1, 32, 0, st>>>(w->part_s, w->part_occ, w->part_s + REDUCE_BLOCKS,
-                                     w->part_occ + REDUCE_BLOCKS, w->part_def, REDUCE_BLOCKS,
-                                     w->pairs, w->moved, n, lo, w->rec);
+    k_level_finish<<<1, REDUCE_BLOCKS, 0, st>>>(w->part_s, w->part_occ, w->part_s + REDUCE_BLOCKS,
+                                                w->part_occ + REDUCE_BLOCKS, w->part_def,
+                                                w->pairs, w->moved, n, lo, w->rec);
     ++launches;
     note_launches(launches);
     w->have_pairs = true;

@@ -1,0 +1,498 @@
+// k_nd.cu -- the d-dimensional quantised step by directional composition
+// (Theorem, Cartesian extension; eqs. nd_transfer_rule, nd_flux_definition).
+//
+// On a periodic grid (d = 2 or 3, dims[0] fastest) with the same
+// one-dimensional transfer rule along every axis:
+//   F_{i+e_m/2} = phi+(q_i) + phi-(q_{i+e_m})
+//   q_i <- q_i - sum_m (F_{i+e_m/2} - F_{i-e_m/2})
+//        = q_i - d (phi+(q_i) - phi-(q_i)) + sum_m (phi+(q_{i-e_m}) - phi-(q_{i+e_m})).
+// Two kernels: one step per launch with warps walking the slowest axis
+// (2-D and 3-D), and K steps per launch in register tiles (2-D).  Updates
+// are summed in 64-bit and checked against int32.
+#include "nd.h"
+#include "tile_step.cuh"
+
+#include <algorithm>
+#include <climits>
+
+namespace fqnm {
+
+namespace {
+
+using tb::EvClosedP;
+using tb::EvTableP;
+using tb::EvTablePM;
+using tb::EvTablePM16;
+
+struct Strides {
+    long long n, nx, ny, nz, sy, sz;
+};
+
+// ---- marching one-step kernels ---------------------------------------------------
+// Each warp owns a strip of 32 consecutive x (lane = column) and walks along
+// the slowest axis, keeping the row below and the current row in registers:
+// every cell is loaded once, its maps are evaluated once, its x neighbours'
+// values arrive by shuffle, and its update is stored once.  The lanes at the
+// strip's two ends (and the columns next to the periodic seam) also load and
+// evaluate the neighbouring column outside the strip.  Rows go in groups of
+// MARCH_G: the group's loads (and edge loads) are issued together, then its
+// maps evaluated, then its updates applied, so that MARCH_G loads and
+// gathers are in flight per warp.  2-D walks y; 3-D walks z with the block's
+// warps on consecutive y rows, exchanging y-edge values through shared
+// memory (the block's first and last warp only supply halo rows).
+
+constexpr int MARCH_G = 8;                // rows per group
+constexpr int MARCH_ROWS = 32;            // rows of the walk per warp (2-D); a multiple of MARCH_G
+
+struct EdgeCols {
+    bool need_l, need_r;
+    long long xl, xr;                     // neighbour columns outside the strip (or across the seam)
+};
+
+__device__ __forceinline__ EdgeCols edge_cols(long long x, long long nx, int lane)
+{
+    EdgeCols e;
+    e.need_l = lane == 0 || x == 0;
+    e.need_r = lane == 31 || x + 1 == nx;
+    e.xl = x > 0 ? x - 1 : nx - 1;
+    e.xr = x + 1 < nx ? x + 1 : 0;
+    return e;
+}
+
+template <class Ev>
+__global__ void __launch_bounds__(256)
+k_march2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long long ny,
+          long long strips, long long chunks, Ev ev, unsigned* __restrict__ err)
+{
+    const int lane = threadIdx.x & 31;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= strips * chunks) return;                 // whole warp
+    const long long strip = wid % strips, chunk = wid / strips;
+    const long long x = strip * 32 + lane;
+    const long long xc = x < nx ? x : nx - 1;           // idle lanes shadow a valid column
+    const EdgeCols e = edge_cols(xc, nx, lane);
+    const long long y0 = chunk * MARCH_ROWS;
+    const long long y1 = y0 + MARCH_ROWS < ny ? y0 + MARCH_ROWS : ny;
+    unsigned acc = 0;
+    bool over = false;
+    int pd, md, qc, pc, mc, plc = 0, mrc = 0;           // row y-1: p; row y: q, p, m, edges
+    {
+        const long long yd = y0 > 0 ? y0 - 1 : ny - 1;
+        ev(__ldg(qin + yd * nx + xc), pd, md, acc);
+        qc = __ldg(qin + y0 * nx + xc);
+        ev(qc, pc, mc, acc);
+        int t;
+        if (e.need_l) ev(__ldg(qin + y0 * nx + e.xl), plc, t, acc);
+        if (e.need_r) ev(__ldg(qin + y0 * nx + e.xr), t, mrc, acc);
+    }
+    for (long long y = y0; y < y1; y += MARCH_G) {
+        int qn[MARCH_G], pn[MARCH_G], mn[MARCH_G], pl[MARCH_G], mr[MARCH_G];
+#pragma unroll
+        for (int g = 0; g < MARCH_G; ++g) {             // rows y+1 .. y+G, loads in flight together
+            long long r = y + 1 + g;
+            if (r >= ny) r -= ny;
+            if (r >= ny) r %= ny;
+            const int* row = qin + r * nx;
+            qn[g] = __ldg(row + xc);
+            pl[g] = e.need_l ? __ldg(row + e.xl) : 0;
+            mr[g] = e.need_r ? __ldg(row + e.xr) : 0;
+        }
+#pragma unroll
+        for (int g = 0; g < MARCH_G; ++g) {
+            int t;
+            ev(qn[g], pn[g], mn[g], acc);
+            if (e.need_l) ev(pl[g], pl[g], t, acc);
+            if (e.need_r) ev(mr[g], t, mr[g], acc);
+        }
+#pragma unroll
+        for (int g = 0; g < MARCH_G; ++g) {             // update row y+g
+            const int q0 = g == 0 ? qc : qn[g - 1];
+            const int p0 = g == 0 ? pc : pn[g - 1];
+            const int m0 = g == 0 ? mc : mn[g - 1];
+            const int pdn = g == 0 ? pd : (g == 1 ? pc : pn[g - 2]);
+            int l = __shfl_up_sync(0xffffffffu, p0, 1);
+            int r = __shfl_down_sync(0xffffffffu, m0, 1);
+            if (e.need_l) l = g == 0 ? plc : pl[g - 1];
+            if (e.need_r) r = g == 0 ? mrc : mr[g - 1];
+            const long long v = (long long)q0 - 2LL * ((long long)p0 - (long long)m0) + l + pdn
+                                - (long long)r - (long long)mn[g];
+            if (x < nx && y + g < y1) {
+                if (v < INT_MIN || v > INT_MAX) over = true;
+                qout[(y + g) * nx + x] = (int)v;
+            }
+        }
+        pd = pn[MARCH_G - 2];
+        qc = qn[MARCH_G - 1];
+        pc = pn[MARCH_G - 1];
+        mc = mn[MARCH_G - 1];
+        plc = pl[MARCH_G - 1];
+        mrc = mr[MARCH_G - 1];
+    }
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+    if (over) atomicOr(err, ERRBIT_OVERFLOW);
+}
+
+constexpr int MARCH3_WARPS = 16;          // 14 rows + 2 halo rows per block
+constexpr int MARCH3_ROWS = MARCH3_WARPS - 2;
+constexpr int MARCH3_SLABS = 32;          // z slabs per block; a multiple of MARCH_G
+
+template <class Ev>
+__global__ void __launch_bounds__(32 * MARCH3_WARPS)
+k_march3d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long long ny,
+          long long nz, long long strips, long long rowblocks, Ev ev, unsigned* __restrict__ err)
+{
+    __shared__ int shp[2][MARCH3_WARPS][32];
+    __shared__ int shm[2][MARCH3_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long b = blockIdx.x;
+    const long long strip = b % strips, rb = (b / strips) % rowblocks, zc = b / (strips * rowblocks);
+    const long long x = strip * 32 + lane;
+    const long long xc = x < nx ? x : nx - 1;
+    const EdgeCols e = edge_cols(xc, nx, lane);
+    // warp w handles row y = rb*ROWS + w - 1 (w = 0 and w = WARPS-1: halo rows)
+    long long y = rb * MARCH3_ROWS + w - 1;
+    const bool owner = w >= 1 && w <= MARCH3_ROWS && y < ny;
+    y = tb::wrap_index(y, ny);
+    const long long sy = nx, sz = nx * ny;
+    const long long z0 = zc * MARCH3_SLABS;
+    const long long z1 = z0 + MARCH3_SLABS < nz ? z0 + MARCH3_SLABS : nz;
+    unsigned acc = 0;
+    bool over = false;
+    int pd, md, qc, pc, mc, plc = 0, mrc = 0;
+    {
+        const long long zd = z0 > 0 ? z0 - 1 : nz - 1;
+        ev(__ldg(qin + zd * sz + y * sy + xc), pd, md, acc);
+        const int* row = qin + z0 * sz + y * sy;
+        qc = __ldg(row + xc);
+        ev(qc, pc, mc, acc);
+        int t;
+        if (e.need_l) ev(__ldg(row + e.xl), plc, t, acc);
+        if (e.need_r) ev(__ldg(row + e.xr), t, mrc, acc);
+    }
+    int s = 0;
+    for (long long z = z0; z < z1; z += MARCH_G) {
+        int qn[MARCH_G], pn[MARCH_G], mn[MARCH_G], pl[MARCH_G], mr[MARCH_G];
+#pragma unroll
+        for (int g = 0; g < MARCH_G; ++g) {
+            long long r = z + 1 + g;
+            if (r >= nz) r -= nz;
+            if (r >= nz) r %= nz;
+            const int* row = qin + r * sz + y * sy;
+            qn[g] = __ldg(row + xc);
+            pl[g] = e.need_l ? __ldg(row + e.xl) : 0;
+            mr[g] = e.need_r ? __ldg(row + e.xr) : 0;
+        }
+#pragma unroll
+        for (int g = 0; g < MARCH_G; ++g) {
+            int t;
+            ev(qn[g], pn[g], mn[g], acc);
+            if (e.need_l) ev(pl[g], pl[g], t, acc);
+            if (e.need_r) ev(mr[g], t, mr[g], acc);
+        }
+#pragma unroll
+        for (int g = 0; g < MARCH_G; ++g, s ^= 1) {     // update slab z+g
+            const int q0 = g == 0 ? qc : qn[g - 1];
+            const int p0 = g == 0 ? pc : pn[g - 1];
+            const int m0 = g == 0 ? mc : mn[g - 1];
+            const int pdn = g == 0 ? pd : (g == 1 ? pc : pn[g - 2]);
+            shp[s][w][lane] = p0;
+            shm[s][w][lane] = m0;
+            __syncthreads();
+            int l = __shfl_up_sync(0xffffffffu, p0, 1);
+            int r = __shfl_down_sync(0xffffffffu, m0, 1);
+            if (e.need_l) l = g == 0 ? plc : pl[g - 1];
+            if (e.need_r) r = g == 0 ? mrc : mr[g - 1];
+            if (owner) {
+                const int pdy = shp[s][w - 1][lane], muy = shm[s][w + 1][lane];
+                const long long v = (long long)q0 - 3LL * ((long long)p0 - (long long)m0) + l + pdy
+                                    + pdn - (long long)r - (long long)muy - (long long)mn[g];
+                if (x < nx && z + g < z1) {
+                    if (v < INT_MIN || v > INT_MAX) over = true;
+                    qout[(z + g) * sz + y * sy + x] = (int)v;
+                }
+            }
+        }
+        pd = pn[MARCH_G - 2];
+        qc = qn[MARCH_G - 1];
+        pc = pn[MARCH_G - 1];
+        mc = mn[MARCH_G - 1];
+        plc = pl[MARCH_G - 1];
+        mrc = mr[MARCH_G - 1];
+    }
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+    if (over) atomicOr(err, ERRBIT_OVERFLOW);
+}
+
+template <class Ev>
+cudaError_t dispatch_march(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                           unsigned* err, cudaStream_t st)
+{
+    const long long nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    const long long strips = (nx + 31) / 32;
+    if (g.d == 2) {
+        const long long chunks = (ny + MARCH_ROWS - 1) / MARCH_ROWS;
+        const long long warps = strips * chunks;
+        const long long blocks = (warps + 7) / 8;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        k_march2d<<<(unsigned)blocks, 256, 0, st>>>(qin, qout, nx, ny, strips, chunks, ev, err);
+    } else {
+        const long long rowblocks = (ny + MARCH3_ROWS - 1) / MARCH3_ROWS;
+        const long long zchunks = (nz + MARCH3_SLABS - 1) / MARCH3_SLABS;
+        const long long blocks = strips * rowblocks * zchunks;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        k_march3d<<<(unsigned)blocks, 32 * MARCH3_WARPS, 0, st>>>(qin, qout, nx, ny, nz, strips,
+                                                                   rowblocks, ev, err);
+    }
+    note_launches();
+    return cudaGetLastError();
+}
+
+// ---- 2-D temporal blocking ------------------------------------------------------
+// A block of WX x WY warps holds a TX x TY tile (TX = 32 WX along x, TY =
+// VY WY along y) in registers: lane l of warp (wx, wy) holds column
+// 32 wx + l, rows VY wy .. VY wy + VY - 1.  The tile starts K cells left of
+// and below its output region and applies K steps; the cells whose
+// dependency cone (within K in x and in y) stayed inside the tile are exact
+// and are written: (TX - 2K) x (TY - 2K) per tile.
+//   x neighbours: shuffles inside a warp; a warp's edge columns (p of lane
+//     31, m of lane 0) through shared memory to the warps left and right;
+//   y neighbours: registers inside a thread; a warp's edge rows (p of the top
+//     row, m of the bottom row) through shared memory to the warps above and
+//     below.
+// Edge arrays are double-buffered: one barrier per step.  The tile's outer
+// cells use a ghost copy of themselves (values outside the exact region,
+// kept on a valid scheme so they cannot trip the range guard).
+
+template <int VY, int WX, int WY>
+struct Tile2dSmem {
+    int xp[2][WX * WY][VY];        // p of lane 31, per row
+    int xm[2][WX * WY][VY];        // m of lane 0, per row
+    int yp[2][WX * WY][32];        // p of the top row, per lane
+    int ym[2][WX * WY][32];        // m of the bottom row, per lane
+};
+
+struct Tile2dArgs {
+    long long nx, ny;
+    int K;
+    long long SX, SY;              // output cells per tile along x and y
+    long long tiles_x;
+};
+
+using tb::wrap_index;           // one conditional add or subtract; a modulo only for tiny grids
+
+template <class Ev, int VY, int WX, int WY>
+__global__ void __launch_bounds__(32 * WX * WY)
+k_step2d_tb(const int* __restrict__ qin, int* __restrict__ qout, Tile2dArgs a, Ev ev,
+            unsigned* __restrict__ err)
+{
+    __shared__ Tile2dSmem<VY, WX, WY> sm;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int wx = w % WX, wy = w / WX;
+    const long long tx = blockIdx.x % a.tiles_x, ty = blockIdx.x / a.tiles_x;
+    const long long x0 = tx * a.SX - a.K, y0 = ty * a.SY - a.K;
+    const int ex = 32 * wx + lane;                      // tile column
+    const long long gx = wrap_index(x0 + ex, a.nx);
+    int q[VY];
+#pragma unroll
+    for (int j = 0; j < VY; ++j)
+        q[j] = __ldg(qin + wrap_index(y0 + VY * wy + j, a.ny) * a.nx + gx);
+
+    unsigned acc = 0;
+    const int wl = wx > 0 ? w - 1 : w, wr = wx < WX - 1 ? w + 1 : w;
+    const int wd = wy > 0 ? w - WX : w, wu = wy < WY - 1 ? w + WX : w;
+    for (int s = 0; s < a.K; ++s) {
+        int p[VY], m[VY];
+#pragma unroll
+        for (int j = 0; j < VY; ++j) ev(q[j], p[j], m[j], acc);
+        const int b = s & 1;
+        if (lane == 31)
+#pragma unroll
+            for (int j = 0; j < VY; ++j) sm.xp[b][w][j] = p[j];
+        if (Ev::HAS_M && lane == 0)
+#pragma unroll
+            for (int j = 0; j < VY; ++j) sm.xm[b][w][j] = m[j];
+        sm.yp[b][w][lane] = p[VY - 1];
+        if (Ev::HAS_M) sm.ym[b][w][lane] = m[0];
+        __syncthreads();
+        // neighbours across warp edges (own value at the tile's outer edge)
+        const int pd0 = wy > 0 ? sm.yp[b][wd][lane] : p[0];
+        const int muT = (Ev::HAS_M && wy < WY - 1) ? sm.ym[b][wu][lane] : m[VY - 1];
+#pragma unroll
+        for (int j = 0; j < VY; ++j) {
+            int pl = __shfl_up_sync(0xffffffffu, p[j], 1);
+            if (lane == 0) pl = wx > 0 ? sm.xp[b][wl][j] : p[j];
+            const int pd = j > 0 ? p[j - 1] : pd0;
+            int d = pl + pd - 2 * p[j];
+            if (Ev::HAS_M) {
+                int mr = __shfl_down_sync(0xffffffffu, m[j], 1);
+                if (lane == 31) mr = wx < WX - 1 ? sm.xm[b][wr][j] : m[j];
+                const int mu = j < VY - 1 ? m[j + 1] : muT;
+                d += 2 * m[j] - mr - mu;
+            }
+            q[j] += d;
+        }
+    }
+    // the exact region: tile cells [K, K + SX) x [K, K + SY)
+    if (ex >= a.K && ex < a.K + a.SX) {
+        const long long ox = tx * a.SX + (ex - a.K);
+        if (ox < a.nx) {
+#pragma unroll
+            for (int j = 0; j < VY; ++j) {
+                const int ey = VY * wy + j;
+                if (ey < a.K || ey >= a.K + a.SY) continue;
+                const long long oy = ty * a.SY + (ey - a.K);
+                if (oy < a.ny) qout[oy * a.nx + ox] = q[j];
+            }
+        }
+    }
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+}
+
+template <class Ev, int VY, int WX, int WY>
+cudaError_t launch_2d(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g, int K,
+                      unsigned* err, cudaStream_t st)
+{
+    constexpr int TX = 32 * WX, TY = VY * WY;
+    if (2 * K >= TX || 2 * K >= TY) return cudaErrorInvalidValue;
+    Tile2dArgs a;
+    a.nx = g.dims[0];
+    a.ny = g.dims[1];
+    a.K = K;
+    a.SX = TX - 2 * K;
+    a.SY = TY - 2 * K;
+    a.tiles_x = (a.nx + a.SX - 1) / a.SX;
+    const long long tiles_y = (a.ny + a.SY - 1) / a.SY;
+    const long long blocks = a.tiles_x * tiles_y;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_step2d_tb<Ev, VY, WX, WY><<<(unsigned)blocks, 32 * WX * WY, 0, st>>>(qin, qout, a, ev, err);
+    note_launches();
+    return cudaGetLastError();
+}
+
+template <class Ev>
+cudaError_t dispatch_2d(const Ev& ev, const NdPlan& p, const int32_t* qin, int32_t* qout,
+                        const NdGrid& g, int K, unsigned* err, cudaStream_t st)
+{
+    switch (p.shape) {
+    case ND_TILE_64x64: return launch_2d<Ev, 16, 2, 4>(ev, qin, qout, g, K, err, st);
+    case ND_TILE_128x64: return launch_2d<Ev, 16, 4, 4>(ev, qin, qout, g, K, err, st);
+    case ND_TILE_64x32: return launch_2d<Ev, 8, 2, 4>(ev, qin, qout, g, K, err, st);
+    case ND_TILE_128x32: return launch_2d<Ev, 8, 4, 4>(ev, qin, qout, g, K, err, st);
+    case ND_TILE_32x128: return launch_2d<Ev, 16, 1, 8>(ev, qin, qout, g, K, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+constexpr int IBLOCK = 256;
+
+__device__ __forceinline__ long long warp_sum64(long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(IBLOCK)
+k_invariants_nd(const int* __restrict__ q, const int* __restrict__ other, Strides g, int d,
+                long long* acc)
+{
+    __shared__ long long sh[3][IBLOCK / 32];
+    long long mass = 0, tv = 0, l1 = 0;
+    const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (x < g.nx) {
+        const long long xr = x + 1 < g.nx ? x + 1 : 0;
+        for (long long z = blockIdx.z; z < g.nz; z += gridDim.z) {
+            const long long zr = z + 1 < g.nz ? z + 1 : 0;
+            for (long long y = blockIdx.y; y < g.ny; y += gridDim.y) {
+                const long long yr = y + 1 < g.ny ? y + 1 : 0;
+                const long long row = z * g.sz + y * g.sy;
+                const long long v = q[row + x];
+                mass += v;
+                long long w = q[row + xr];
+                tv += w > v ? w - v : v - w;
+                if (d >= 2) {
+                    w = q[z * g.sz + yr * g.sy + x];
+                    tv += w > v ? w - v : v - w;
+                }
+                if (d >= 3) {
+                    w = q[zr * g.sz + y * g.sy + x];
+                    tv += w > v ? w - v : v - w;
+                }
+                if (other) {
+                    const long long o = other[row + x];
+                    l1 += o > v ? o - v : v - o;
+                }
+            }
+        }
+    }
+    mass = warp_sum64(mass);
+    tv = warp_sum64(tv);
+    l1 = warp_sum64(l1);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][w] = mass; sh[1][w] = tv; sh[2][w] = l1; }
+    __syncthreads();
+    if (w == 0) {
+        for (int k = 0; k < 3; ++k) {
+            long long t = lane < IBLOCK / 32 ? sh[k][lane] : 0;
+            t = warp_sum64(t);
+            if (lane == 0 && t != 0) atomicAdd((unsigned long long*)(acc + k), (unsigned long long)t);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_step_nd(const RuleView& r, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                           unsigned* err, cudaStream_t st)
+{
+    if (g.d < 2 || g.d > 3 || g.cells() <= 0) return cudaErrorInvalidValue;
+    if (r.evaluator == EVAL_CLOSED_FORM && !r.has_m)
+        return dispatch_march(EvClosedP{r.cf, r.lo, r.span}, qin, qout, g, err, st);
+    if (!r.has_m) return dispatch_march(EvTableP{r.tabp, r.lo, r.span}, qin, qout, g, err, st);
+    if (r.tab16) return dispatch_march(EvTablePM16{r.tab16, r.lo, r.span}, qin, qout, g, err, st);
+    return dispatch_march(EvTablePM{r.tab2, r.lo, r.span}, qin, qout, g, err, st);
+}
+
+int nd_tile_x(int shape)
+{
+    switch (shape) {
+    case ND_TILE_64x64: case ND_TILE_64x32: return 64;
+    case ND_TILE_128x64: case ND_TILE_128x32: return 128;
+    case ND_TILE_32x128: return 32;
+    default: return 0;
+    }
+}
+
+int nd_tile_y(int shape)
+{
+    switch (shape) {
+    case ND_TILE_64x64: case ND_TILE_128x64: return 64;
+    case ND_TILE_64x32: case ND_TILE_128x32: return 32;
+    case ND_TILE_32x128: return 128;
+    default: return 0;
+    }
+}
+
+cudaError_t launch_step2d_tb(const RuleView& r, const NdPlan& p, const int32_t* qin,
+                             int32_t* qout, const NdGrid& g, int K, unsigned* err,
+                             cudaStream_t st)
+{
+    if (g.d != 2 || K < 1) return cudaErrorInvalidValue;
+    if (r.evaluator == EVAL_CLOSED_FORM && !r.has_m)
+        return dispatch_2d(EvClosedP{r.cf, r.lo, r.span}, p, qin, qout, g, K, err, st);
+    if (!r.has_m) return dispatch_2d(EvTableP{r.tabp, r.lo, r.span}, p, qin, qout, g, K, err, st);
+    if (r.tab16) return dispatch_2d(EvTablePM16{r.tab16, r.lo, r.span}, p, qin, qout, g, K, err, st);
+    return dispatch_2d(EvTablePM{r.tab2, r.lo, r.span}, p, qin, qout, g, K, err, st);
+}
+
+cudaError_t launch_invariants_nd(const int32_t* q, const int32_t* other, const NdGrid& gr,
+                                 long long* acc, cudaStream_t st)
+{
+    Strides g{gr.cells(), gr.dims[0], gr.dims[1], gr.dims[2], gr.dims[0], gr.dims[0] * gr.dims[1]};
+    const dim3 grid((unsigned)((g.nx + IBLOCK - 1) / IBLOCK),
+                    (unsigned)std::min<long long>(g.ny, 1024), (unsigned)std::min<long long>(g.nz, 64));
+    k_invariants_nd<<<grid, IBLOCK, 0, st>>>(q, other, g, gr.d, acc);
+    note_launches();
+    return cudaGetLastError();
+}
+
+}  // namespace fqnm

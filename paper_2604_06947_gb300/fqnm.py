@@ -29,7 +29,7 @@ ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
 BOUNDARY = {"periodic": 0, "transmissive": 1}
 OPTION = {"kernel": 0, "layout": 1, "cells_per_thread": 2, "block": 3, "k": 4,
           "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9,
-          "pdl": 10, "pack16": 11, "quantise_mask": 12}
+          "pdl": 10, "pack16": 11, "quantise_mask": 12, "nd_tile": 13}
 
 
 class FqnmError(RuntimeError):
@@ -104,6 +104,7 @@ PROTOTYPES = {
     "fqnm_invariants_noalloc": (_st, [_vp, _vp, C.c_size_t, C.c_int,
                                       C.POINTER(C.c_int64), _vp]),
     "fqnm_get_size": (_st, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "fqnm_set_grid": (_st, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
     "fqnm_hopf_lax": (_st, [_vp, C.c_size_t, _vp, _vp, C.c_size_t, C.c_double, _vp, _vp,
                             C.c_int, _vp]),
     "fqnm_level_step": (_st, [_vp, C.POINTER(fqnm_level_stats_t)]),
@@ -349,6 +350,12 @@ def fqnm_invariants_noalloc(q_dev, n: int, other_dev=None, boundary: str = "peri
     _check(load().fqnm_invariants_noalloc(_dptr(q_dev), _dptr(other_dev) or None, n,
                                           BOUNDARY[boundary], out, _stream(stream)))
     return out[0], out[1], out[2]
+
+
+def fqnm_set_grid(h: int, dims) -> None:
+    """dims in x-fastest order, e.g. (nx, ny) or (nx, ny, nz)."""
+    arr = (C.c_size_t * 3)(*([int(v) for v in dims] + [1] * (3 - len(dims))))
+    _check(load().fqnm_set_grid(h, len(dims), arr))
 
 
 def fqnm_hopf_lax(x, y, U0y, t: float, nx: Optional[int] = None, ny: Optional[int] = None,
@@ -651,6 +658,11 @@ class Solver:
 
     def invariants(self, other: Optional["Solver"] = None):
         return fqnm_invariants(self.h, other.h if other else None)
+
+    def set_grid(self, dims):
+        """Periodic Cartesian grid, dims x-fastest (call before load)."""
+        fqnm_set_grid(self.h, dims)
+        return self
 
     def level_step(self) -> dict:
         return fqnm_level_step(self.h)

@@ -182,6 +182,34 @@ def sine_candidates(ny: int, images=(-1, 0, 1)):
     return y, U0
 
 
+def burgers_nd_problem(dims=(1024, 1024), delta: float = 2.0 ** -16, courant: float = 0.4,
+                       steps: int = 1000, seed: int = BASE_SEED + 5) -> ScalarProblem:
+    """Burgers on a periodic d-dimensional grid (dims x-fastest), LF with
+    alpha = 1.3 on every axis, d * nu = courant: u0 = 0.5 + 0.5 prod_m
+    sin(2 pi (x_m + phase_m)) + seeded steps along x (the one-dimensional
+    Burgers family's 16 random levels), so u0 lies in [-0.3, 1.3].
+    p.u0 is flat, x fastest; p.dims holds the shape."""
+    d = len(dims)
+    nx = dims[0]
+    dx = 1.0 / nx
+    dt = courant / d * dx / BURGERS_ALPHA
+    n = int(np.prod(dims))
+    p = ScalarProblem("burgers_%dd" % d, "burgers_lf", n, delta, dx, dt, steps,
+                      alpha=BURGERS_ALPHA)
+    rng = SplitMix64(seed)
+    phases = [rng.uniform() for _ in range(d)]
+    axes = [(np.arange(m) + 0.5) / m for m in dims]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")          # (.., y, x)
+    prod = np.ones(grids[0].shape)
+    for m in range(d):
+        prod = prod * np.sin(2.0 * np.pi * (grids[d - 1 - m] + phases[m]))
+    steps_x = burgers_steps_u0(nx, seed + 1) - (0.5 + 0.5 * np.sin(2.0 * np.pi * axes[0]))
+    u0 = 0.5 + 0.5 * prod + 0.3 * np.clip(steps_x / 0.3, -1.0, 1.0)
+    p.u0 = np.clip(u0, -0.3, 1.3).reshape(-1)
+    p.dims = tuple(dims)
+    return p
+
+
 def high_frequency_problem(n: int = 1 << 24, delta: float = 2.0 ** -20,
                            courant: float = 0.9, steps: int = 2000,
                            seed: int = BASE_SEED + 2,

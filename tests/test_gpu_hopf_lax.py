@@ -44,6 +44,13 @@ def test_ties_go_to_the_smallest_index_and_nan_candidates():
     assert list(idx) == [1, 3, 1]                  # 0.375: equidistant from 0.25 and 0.5
     u, idx = F.fqnm_hopf_lax(np.array([0.1]), np.array([0.0]), np.array([np.nan]), 1.0)
     assert idx[0] == -1 and np.isnan(u[0])
+    # infinities and NaN among finite candidates: NaN is never the minimum,
+    # -inf always is, +inf only loses
+    y = np.array([0.0, 0.1, 0.2, 0.3])
+    for U, want in (([np.nan, 1.0, 2.0, np.inf], 1), ([1.0, -np.inf, np.nan, 0.5], 1),
+                    ([np.inf, np.inf, np.nan, np.nan], -1), ([-0.0, 0.0, 0.0, 1.0], 0)):
+        u, idx = F.fqnm_hopf_lax(np.array([0.0]), y, np.array(U), 1e6)
+        assert idx[0] == want, U
 
 
 def test_device_variant_dense_grid_sampled():

@@ -1,0 +1,120 @@
+"""Parity of the CUDA d-dimensional step (Theorem, Cartesian extension by
+directional composition) with the oracle, bit for bit, on 2-D and 3-D
+periodic grids with ragged sizes; exact conservation and the axis-summed
+total variation."""
+import numpy as np
+import pytest
+
+from paper_2604_06947_gb300 import fqnm as F
+from paper_2604_06947_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def solver_for(p, **opt):
+    s = F.Solver.for_problem(p, **opt)
+    s.set_grid(p.dims)
+    return s
+
+
+def tv_nd(q):
+    return int(sum(np.abs(np.roll(q, -1, axis=a) - q).sum() for a in range(q.ndim)))
+
+
+@pytest.mark.parametrize("dims", [(96, 80), (33, 7), (24, 20, 18), (5, 3, 31)])
+def test_burgers_nd_bit_exact(orc, dims):
+    p = I.burgers_nd_problem(dims)
+    shape = dims[::-1]
+    q0 = orc.quantise(p.u0, p.delta).reshape(shape)
+    s = solver_for(p).load(q0.reshape(-1))
+    q = q0.copy()
+    for k in (1, 7, 40):
+        s.step(k)
+        q = orc.step_nd(q, "burgers_lf", p.delta, p.dx, p.dt, k, alpha=p.alpha)
+        assert np.array_equal(s.state().reshape(shape), q), k
+    inv = s.invariants()
+    assert inv["mass"][0] == int(q0.sum())
+    assert inv["tv"][0] == tv_nd(q)
+    s.close()
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_every_2d_plan_bit_exact(orc, tile, k):
+    """Every register tile and several K (ragged step counts), on a ragged
+    grid and on a grid smaller than one tile."""
+    for dims in ((150, 70), (9, 11)):
+        p = I.burgers_nd_problem(dims)
+        shape = dims[::-1]
+        q0 = orc.quantise(p.u0, p.delta).reshape(shape)
+        s = solver_for(p, nd_tile=tile, k=k).load(q0.reshape(-1))
+        s.step(10)
+        want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 10, alpha=p.alpha)
+        assert np.array_equal(s.state().reshape(shape), want), dims
+        s.close()
+
+
+@pytest.mark.parametrize("dims", [(100, 60), (1, 5), (31, 1), (33, 150), (64, 129), (7, 3, 2),
+                                  (40, 30, 70)])
+def test_one_step_marching_kernel(orc, dims):
+    """The one-step kernels (2-D: warps walk y; 3-D: blocks of rows walk z)
+    on shapes narrower than a warp, with one row, with several walk chunks
+    and ragged strips."""
+    p = I.burgers_nd_problem(dims)
+    shape = dims[::-1]
+    q0 = orc.quantise(p.u0, p.delta).reshape(shape)
+    s = solver_for(p, kernel=1).load(q0.reshape(-1))
+    s.step(9)
+    want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 9, alpha=p.alpha)
+    assert np.array_equal(s.state().reshape(shape), want)
+    s.close()
+
+
+def test_linear_upwind_closed_form_2d(orc):
+    """Upwind a = 1 at nu = 0.45 per axis (d nu = 0.9): phi+ = R(9 q / 20),
+    the verified closed form replaces the table."""
+    p = I.burgers_nd_problem((64, 48))
+    p.flux, p.a, p.alpha = "linear_upwind", 1.0, 0.0
+    p.dt = 0.45 * p.dx
+    q0 = orc.quantise(p.u0, p.delta).reshape(48, 64)
+    s = solver_for(p).load(q0.reshape(-1))
+    s.step(30)
+    want = orc.step_nd(q0, "linear_upwind", p.delta, p.dx, p.dt, 30, a=1.0)
+    assert np.array_equal(s.state().reshape(48, 64), want)
+    s.close()
+
+
+def test_full_size_2d_grid(orc):
+    """2048 x 2048 cells (16 MiB of state), 20 steps, against the oracle."""
+    p = I.burgers_nd_problem((2048, 2048))
+    q0 = orc.quantise(p.u0, p.delta).reshape(2048, 2048)
+    s = solver_for(p).load(q0.reshape(-1))
+    s.step(20)
+    want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 20, alpha=p.alpha)
+    assert np.array_equal(s.state().reshape(2048, 2048), want)
+    assert s.invariants()["mass"][0] == int(q0.sum())
+    s.close()
+
+
+def test_grid_errors():
+    p = I.burgers_nd_problem((16, 16))
+    s = F.Solver.for_problem(p)
+    with pytest.raises(F.FqnmError):
+        F.fqnm_set_grid(s.h, (16, 0))
+    s.set_grid((16, 16))
+    with pytest.raises(F.FqnmError):
+        s.load(np.zeros(100, dtype=np.int32))           # not 16 x 16 cells
+    s.load(np.zeros(256, dtype=np.int32))
+    with pytest.raises(F.FqnmError):
+        F.fqnm_set_grid(s.h, (16, 16))                  # after loading
+    s.close()
+    q = I.burgers_nd_problem((16, 16))
+    q.dt = 0.5 * q.dx / q.alpha                          # nu = 0.5 per axis
+    s = F.Solver.for_problem(q)
+    F.fqnm_set_grid(s.h, (16, 16))                       # d nu = 1: allowed
+    s.close()
+    q.dt = 0.6 * q.dx / q.alpha
+    s = F.Solver.for_problem(q)
+    with pytest.raises(F.FqnmError):
+        F.fqnm_set_grid(s.h, (16, 16))                   # d nu = 1.2
+    s.close()
