@@ -414,7 +414,7 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_GRAPH: s->use_graph = value != 0; break;
     case FQNM_OPT_PACK16: s->pack16 = value != 0; break;
     case FQNM_OPT_ND_TILE:
-        if (value < 0 || value > ND_TILE_32x128) return set_error(FQNM_ERR_ARG, "tile shape 0..5");
+        if (value < 0 || value > ND_WALK) return set_error(FQNM_ERR_ARG, "2-D plan 0..6");
         s->opt_nd_tile = (int)value; break;
     case FQNM_OPT_QUANTISE_MASK:
         if (value < 0 || value > 7) return set_error(FQNM_ERR_ARG, "mask must be 0..7");
@@ -880,10 +880,18 @@ static NdPlan nd_plan(const fqnm_solver* s)
 {
     NdPlan p;
     p.blocked = s->grid.d == 2 && s->opt_kernel != 1;
-    if (s->opt_nd_tile) p.shape = s->opt_nd_tile;
-    const int lim = std::min(nd_tile_x(p.shape), nd_tile_y(p.shape)) / 2 - 1;
+    p.walk = s->opt_nd_tile == ND_WALK;
+    if (s->opt_nd_tile && !p.walk) p.shape = s->opt_nd_tile;
+    const int lim = p.walk ? 8 : std::min(nd_tile_x(p.shape), nd_tile_y(p.shape)) / 2 - 1;
     p.k = s->opt_k > 0 ? std::min(s->opt_k, lim) : std::min(4, lim);
     return p;
+}
+
+// The walk supports K in {1, 2, 3, 4, 6, 8}: the largest of them <= k.
+static int walk_k(int k)
+{
+    while (k > 1 && !walk_k_supported(k)) --k;
+    return k;
 }
 
 static fqnm_status step_scalar(fqnm_solver* s, uint64_t k)
@@ -894,7 +902,12 @@ static fqnm_status step_scalar(fqnm_solver* s, uint64_t k)
         const NdPlan np = nd_plan(s);
         uint64_t done = 0;
         while (done < k) {
-            if (np.blocked) {
+            if (np.blocked && np.walk) {
+                const int kk = walk_k((int)std::min<uint64_t>((uint64_t)np.k, k - done));
+                CK(launch_walk2d(s->rule, (const int32_t*)s->q[s->cur], (int32_t*)s->q[1 - s->cur],
+                                 s->grid, kk, s->d_err, s->stream));
+                done += kk;
+            } else if (np.blocked) {
                 const int kk = (int)std::min<uint64_t>((uint64_t)np.k, k - done);
                 CK(launch_step2d_tb(s->rule, np, (const int32_t*)s->q[s->cur],
                                     (int32_t*)s->q[1 - s->cur], s->grid, kk, s->d_err, s->stream));

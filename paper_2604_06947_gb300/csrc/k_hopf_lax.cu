@@ -14,7 +14,7 @@
 // reduces each row's (value, index) pairs.  FP64-bound: the 4 FP64
 // operations of an evaluation run on the FP64 pipe (2 per SM per cycle on
 // this part); the comparison runs on the integer pipe, on keys that order
-// as the doubles do (-0 folded onto +0, NaN above every number).
+// as the doubles do (-0 folded onto +0, NaN never taken).
 #include "fqnm_internal.h"
 #include "hopf_lax.h"
 
@@ -26,17 +26,20 @@ namespace {
 
 constexpr int HL_ROWS = 4;
 constexpr int HL_THREADS = 256;
-constexpr long long KEY_INF = 0x7ff0000000000000LL;     // key of +inf (and its bits)
-constexpr long long KEY_NAN = 0x7fffffffffffffffLL;     // above every number
+constexpr long long KEY_INF = 0x7ff0000000000000LL;     // key of +inf (its bits)
+constexpr long long KEY_NEG_INF = (long long)0x8010000000000000ULL;   // key of -inf
 
-// An int64 that orders as the double does: a < b <=> key(a) < key(b) and
-// a == b <=> key(a) == key(b) for non-NaN a, b.
+// An int64 that orders as the double does: for non-NaN a, b,
+// a < b <=> key(a) < key(b) and a == b <=> key(a) == key(b) (-0 and +0
+// both map to 0).  Non-negative doubles keep their bits; negative ones map
+// to (bits ^ 0x7fff...f) + 1.  A NaN maps above KEY_INF (positive sign) or
+// below KEY_NEG_INF (negative sign), so `key < best && key >= KEY_NEG_INF`
+// never takes a NaN.  All integer operations, off the FP64 pipe.
 __device__ __forceinline__ long long order_key(double v)
 {
-    long long b = __double_as_longlong(v);
-    if ((b & KEY_NAN) > KEY_INF) return KEY_NAN;           // NaN
-    if (b == (long long)0x8000000000000000ULL) b = 0;       // -0 -> +0
-    return b >= 0 ? b : b ^ KEY_NAN;
+    const long long b = __double_as_longlong(v);
+    const long long m = b >> 63;                          // 0 or -1
+    return (b ^ (m & 0x7fffffffffffffffLL)) - m;
 }
 
 __global__ void __launch_bounds__(HL_THREADS)
@@ -63,7 +66,7 @@ k_hopf_lax(const double* __restrict__ x, long long nx, const double* __restrict_
         for (int r = 0; r < HL_ROWS; ++r) {
             const double d = __dsub_rn(xr[r], yj);
             const long long o = order_key(__dadd_rn(Uj, __dmul_rn(__dmul_rn(d, d), inv2t)));
-            if (o < best[r]) {                          // first minimum of this lane
+            if (o < best[r] && o >= KEY_NEG_INF) {      // first minimum of this lane
                 best[r] = o;
                 bj[r] = j;
             }

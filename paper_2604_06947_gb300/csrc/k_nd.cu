@@ -383,6 +383,135 @@ cudaError_t dispatch_2d(const Ev& ev, const NdPlan& p, const int32_t* qin, int32
     }
 }
 
+// ---- 2-D temporal walk ------------------------------------------------------------
+// A warp holds a strip of 64 columns (lane l: columns 2l and 2l+1) and walks
+// y, applying K steps as a pipeline: at input row i, level t+1 produces row
+// i-t-1 from level t's rows i-t-2, i-t-1 (kept in registers) and i-t (just
+// produced).  Inside a lane the two columns see each other directly; across
+// lanes one shuffle per cell.  The strip's two outer columns take ghost
+// copies of themselves, so after K levels columns [K, 64-K) are exact, and
+// rows [y0, y1) are exact once the walk has read rows y0-K .. y1+K-1.  No
+// shared memory and no barrier; row loads are issued WALK_AHEAD rows ahead.
+
+constexpr int WALK_COLS = 64;
+
+constexpr int WALK_AHEAD = 4;             // rows loaded ahead of the walk
+
+template <class Ev, int K>
+__global__ void __launch_bounds__(256)
+k_walk2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long long ny,
+         long long strips, long long chunks, long long R, Ev ev, unsigned* __restrict__ err)
+{
+    constexpr int SW = WALK_COLS - 2 * K;               // output columns per strip
+    const int lane = threadIdx.x & 31;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= strips * chunks) return;                 // whole warp
+    const long long strip = wid % strips, chunk = wid / strips;
+    const long long xs = strip * SW - K;                // column of strip index 0
+    const long long xa = wrap_index(xs + 2 * lane, nx), xb = wrap_index(xs + 2 * lane + 1, nx);
+    const long long y0 = chunk * R, y1 = y0 + R < ny ? y0 + R : ny;
+    unsigned acc = 0;
+
+    // level windows: center row (q, p, m) and the p of the row below, two columns
+    int qC[K][2], pC[K][2], mC[K][2], pD[K][2];
+    {
+        const int* row = qin + wrap_index(y0 - K - 1, ny) * nx;
+        const int a = __ldg(row + xa), b = __ldg(row + xb);
+        int pa, ma, pb, mb;
+        ev(a, pa, ma, acc);
+        ev(b, pb, mb, acc);
+#pragma unroll
+        for (int t = 0; t < K; ++t) {                   // ghosts: never reach an output
+            qC[t][0] = a; pC[t][0] = pa; mC[t][0] = ma; pD[t][0] = pa;
+            qC[t][1] = b; pC[t][1] = pb; mC[t][1] = mb; pD[t][1] = pb;
+        }
+    }
+    // rows i .. i+WALK_AHEAD-1 in flight
+    int fa[WALK_AHEAD], fb[WALK_AHEAD];
+#pragma unroll
+    for (int a = 0; a < WALK_AHEAD; ++a) {
+        const int* row = qin + wrap_index(y0 - K + a, ny) * nx;
+        fa[a] = __ldg(row + xa);
+        fb[a] = __ldg(row + xb);
+    }
+    const int ca = 2 * lane, cb = 2 * lane + 1;          // strip column indices
+    const long long oa = strip * SW + (ca - K), ob = strip * SW + (cb - K);
+    const bool wa = ca >= K && ca < WALK_COLS - K && oa < nx;
+    const bool wb = cb >= K && cb < WALK_COLS - K && ob < nx;
+    for (long long i = y0 - K; i < y1 + K; ++i) {
+        int nq[2] = {fa[0], fb[0]};
+#pragma unroll
+        for (int a = 0; a + 1 < WALK_AHEAD; ++a) {
+            fa[a] = fa[a + 1];
+            fb[a] = fb[a + 1];
+        }
+        {
+            const int* row = qin + wrap_index(i + WALK_AHEAD, ny) * nx;
+            fa[WALK_AHEAD - 1] = __ldg(row + xa);
+            fb[WALK_AHEAD - 1] = __ldg(row + xb);
+        }
+        int np[2], nm[2];
+        ev(nq[0], np[0], nm[0], acc);
+        ev(nq[1], np[1], nm[1], acc);
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            int pl = __shfl_up_sync(0xffffffffu, pC[t][1], 1);
+            int mr = __shfl_down_sync(0xffffffffu, mC[t][0], 1);
+            if (lane == 0) pl = pC[t][0];               // ghost of the strip's first column
+            if (lane == 31) mr = mC[t][1];              // ghost of the strip's last column
+            const int v0 = qC[t][0] - 2 * (pC[t][0] - mC[t][0]) + pl + pD[t][0] - mC[t][1] - nm[0];
+            const int v1 = qC[t][1] - 2 * (pC[t][1] - mC[t][1]) + pC[t][0] + pD[t][1] - mr - nm[1];
+            pD[t][0] = pC[t][0]; qC[t][0] = nq[0]; pC[t][0] = np[0]; mC[t][0] = nm[0];
+            pD[t][1] = pC[t][1]; qC[t][1] = nq[1]; pC[t][1] = np[1]; mC[t][1] = nm[1];
+            nq[0] = v0;
+            nq[1] = v1;
+            if (t < K - 1) {
+                ev(nq[0], np[0], nm[0], acc);
+                ev(nq[1], np[1], nm[1], acc);
+            }
+        }
+        const long long r = i - K;                      // level-K row
+        if (r >= y0 && r < y1) {
+            if (wa) qout[r * nx + oa] = nq[0];
+            if (wb) qout[r * nx + ob] = nq[1];
+        }
+    }
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+}
+
+template <class Ev, int K>
+cudaError_t launch_walk(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                        unsigned* err, cudaStream_t st)
+{
+    const long long nx = g.dims[0], ny = g.dims[1];
+    const long long strips = (nx + (WALK_COLS - 2 * K) - 1) / (WALK_COLS - 2 * K);
+    // rows per warp: enough warps to fill every SM (about 24 each), at most 256
+    const long long target = 152LL * 24;
+    long long R = (ny * strips + target - 1) / target;
+    R = R < 16 ? 16 : (R > 256 ? 256 : R);
+    const long long chunks = (ny + R - 1) / R;
+    const long long blocks = (strips * chunks + 7) / 8;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_walk2d<Ev, K><<<(unsigned)blocks, 256, 0, st>>>(qin, qout, nx, ny, strips, chunks, R, ev, err);
+    note_launches();
+    return cudaGetLastError();
+}
+
+template <class Ev>
+cudaError_t dispatch_walk(const Ev& ev, int K, const int32_t* qin, int32_t* qout,
+                          const NdGrid& g, unsigned* err, cudaStream_t st)
+{
+    switch (K) {
+    case 1: return launch_walk<Ev, 1>(ev, qin, qout, g, err, st);
+    case 2: return launch_walk<Ev, 2>(ev, qin, qout, g, err, st);
+    case 3: return launch_walk<Ev, 3>(ev, qin, qout, g, err, st);
+    case 4: return launch_walk<Ev, 4>(ev, qin, qout, g, err, st);
+    case 6: return launch_walk<Ev, 6>(ev, qin, qout, g, err, st);
+    case 8: return launch_walk<Ev, 8>(ev, qin, qout, g, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 constexpr int IBLOCK = 256;
 
 __device__ __forceinline__ long long warp_sum64(long long v)
@@ -482,6 +611,19 @@ cudaError_t launch_step2d_tb(const RuleView& r, const NdPlan& p, const int32_t* 
     if (!r.has_m) return dispatch_2d(EvTableP{r.tabp, r.lo, r.span}, p, qin, qout, g, K, err, st);
     if (r.tab16) return dispatch_2d(EvTablePM16{r.tab16, r.lo, r.span}, p, qin, qout, g, K, err, st);
     return dispatch_2d(EvTablePM{r.tab2, r.lo, r.span}, p, qin, qout, g, K, err, st);
+}
+
+bool walk_k_supported(int K) { return K == 1 || K == 2 || K == 3 || K == 4 || K == 6 || K == 8; }
+
+cudaError_t launch_walk2d(const RuleView& r, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                          int K, unsigned* err, cudaStream_t st)
+{
+    if (g.d != 2 || !walk_k_supported(K)) return cudaErrorInvalidValue;
+    if (r.evaluator == EVAL_CLOSED_FORM && !r.has_m)
+        return dispatch_walk(EvClosedP{r.cf, r.lo, r.span}, K, qin, qout, g, err, st);
+    if (!r.has_m) return dispatch_walk(EvTableP{r.tabp, r.lo, r.span}, K, qin, qout, g, err, st);
+    if (r.tab16) return dispatch_walk(EvTablePM16{r.tab16, r.lo, r.span}, K, qin, qout, g, err, st);
+    return dispatch_walk(EvTablePM{r.tab2, r.lo, r.span}, K, qin, qout, g, err, st);
 }
 
 cudaError_t launch_invariants_nd(const int32_t* q, const int32_t* other, const NdGrid& gr,

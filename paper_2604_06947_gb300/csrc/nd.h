@@ -20,9 +20,10 @@ cudaError_t launch_step_nd(const RuleView& r, const int32_t* qin, int32_t* qout,
 
 // 2-D temporal-blocked plans: tile shape (x by y cells) and K steps per launch.
 enum NdTile { ND_TILE_64x64 = 1, ND_TILE_128x64 = 2, ND_TILE_64x32 = 3, ND_TILE_128x32 = 4,
-              ND_TILE_32x128 = 5 };
+              ND_TILE_32x128 = 5, ND_WALK = 6 };
 struct NdPlan {
-    int blocked = 0;              // 0: one step per launch (k_step_nd)
+    int blocked = 0;              // 0: one step per launch (walking kernels)
+    int walk = 0;                 // blocked: 1 pipelined walk along y, 0 register tiles
     int shape = ND_TILE_64x32;
     int k = 4;
 };
@@ -33,6 +34,12 @@ int nd_tile_y(int shape);
 cudaError_t launch_step2d_tb(const RuleView& r, const NdPlan& p, const int32_t* qin,
                              int32_t* qout, const NdGrid& g, int K, unsigned* err,
                              cudaStream_t st);
+
+// K steps of eq. nd_transfer_rule on a 2-D grid in one launch by a pipelined
+// walk along y (K in {1, 2, 3, 4, 6, 8}).
+bool walk_k_supported(int K);
+cudaError_t launch_walk2d(const RuleView& r, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                          int K, unsigned* err, cudaStream_t st);
 
 // mass, TV summed over the axes (periodic faces), l1 to other (may be null),
 // added to acc[0..2].

@@ -38,12 +38,13 @@ def test_burgers_nd_bit_exact(orc, dims):
     s.close()
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
-@pytest.mark.parametrize("k", [1, 3, 7])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("k", [1, 3, 4, 7, 8])
 def test_every_2d_plan_bit_exact(orc, tile, k):
-    """Every register tile and several K (ragged step counts), on a ragged
-    grid and on a grid smaller than one tile."""
-    for dims in ((150, 70), (9, 11)):
+    """Every register tile and the pipelined walk (6), several K
+    (ragged step counts; the walk rounds 7 down to 6), on a ragged grid, a
+    grid smaller than one strip and one with a single row."""
+    for dims in ((150, 70), (9, 11), (130, 1), (1, 40)):
         p = I.burgers_nd_problem(dims)
         shape = dims[::-1]
         q0 = orc.quantise(p.u0, p.delta).reshape(shape)
