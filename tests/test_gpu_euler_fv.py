@@ -64,6 +64,46 @@ def test_sod_65k_first_2000_steps_bit_exact(orc):
     s.close()
 
 
+@pytest.mark.parametrize("n,checkpoints", [(1 << 20, (50, 100, 200)), (1 << 22, (10, 20))])
+def test_sod_large_grids_first_steps_bit_exact(orc, n, checkpoints):
+    """The two large Sod grids (2^20 and 2^22 cells): every integer state
+    equal to the oracle's at each checkpoint of the first steps, with exact
+    boundary-flux accounting."""
+    p = I.sod_problem(n=n)
+    q0 = sod_q0(p)
+    s = euler_solver(p).load(q0)
+    q, done, bf_total = q0.copy(), 0, np.zeros(3, dtype=np.int64)
+    for c in checkpoints:
+        s.step(c - done)
+        q, bf = orc.euler_step(q, p.gamma, p.delta, p.dx, p.dt, c - done)
+        bf_total += bf
+        done = c
+        assert np.array_equal(s.state(), q), c
+    assert s.invariants()["boundary_flux"] == list(bf_total)
+    s.close()
+
+
+def test_sod_1m_long_run_conservation_and_density_error(orc):
+    """2^20 cells for a tenth of the run (about 92k steps, t = 0.02): beyond
+    the oracle's window, all three totals balance exactly against the
+    counted boundary transfer, and the density stays close to the exact
+    Riemann solution."""
+    p = I.sod_problem(n=1 << 20)
+    k = p.steps // 10
+    q0 = sod_q0(p)
+    s = euler_solver(p).load(q0)
+    s.step(k)
+    inv = s.invariants()
+    for c in range(3):
+        assert inv["mass"][c] == int(q0[c].sum()) - inv["boundary_flux"][c]
+    u = s.observe()
+    x = I.cell_centres(p.n)
+    rex, _, _ = orc.riemann_sample(G, I.SOD_LEFT, I.SOD_RIGHT, 0.5, k * p.dt, x)
+    l1 = p.dx * np.abs(u[0] - rex).sum()
+    assert 0 < l1 < 1e-3, l1
+    s.close()
+
+
 def test_sod_65k_full_run_density_error_and_conservation(orc):
     """Full run to t = 0.2 at 2^16 cells (57,672 steps): beyond the oracle's
     2000-step parity window, check exact conservation with boundary
