@@ -383,3 +383,13 @@ def test_level_entropy_log_count(orc):
     q = np.array([0, 0, 0, 1])
     want = -(0.75 * np.log(0.75) + 0.25 * np.log(0.25))
     assert abs(orc.level_entropy(q) - want) < 1e-15
+
+
+def test_invariants_hand_worked(orc):
+    """mass, TV and l1 of small states worked by hand: periodic TV includes
+    the wrap face, transmissive TV does not."""
+    q = np.array([1, 4, 2])
+    assert tuple(orc.invariants(q)) == (7, 3 + 2 + 1, 0)
+    assert tuple(orc.invariants(q, np.array([0, 6, 2]))) == (7, 6, 1 + 2 + 0)
+    assert tuple(orc.invariants(q, boundary="transmissive")) == (7, 3 + 2, 0)
+    assert tuple(orc.invariants(np.array([-5]))) == (-5, 0, 0)
