@@ -717,7 +717,7 @@ static fqnm_status state_range(fqnm_solver* s, const void* q, int64_t* lo, int64
 
 static fqnm_status build_for_state(fqnm_solver* s, const void* q)
 {
-    int64_t lo, hi;
+    int64_t lo = 0, hi = 0;
     fqnm_status st = state_range(s, q, &lo, &hi);
     if (st != FQNM_OK) return st;
     if (s->user_table) {
@@ -1179,7 +1179,7 @@ extern "C" fqnm_status fqnm_level_step(fqnm_solver* s, fqnm_level_stats_t* out)
     if (st != FQNM_OK) return st;
     const int32_t* qn = level_snap(s->levels);
     const int32_t* qn1 = (const int32_t*)s->q[s->cur];
-    int64_t lo0, hi0, lo1, hi1;
+    int64_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
     st = state_range(s, qn, &lo0, &hi0);
     if (st != FQNM_OK) return st;
     st = state_range(s, qn1, &lo1, &hi1);
@@ -1235,7 +1235,7 @@ extern "C" fqnm_status fqnm_level_histogram(fqnm_solver* s, int64_t* lo, int64_t
     if (st != FQNM_OK) return st;
     st = sync_and_check(s);
     if (st != FQNM_OK) return st;
-    int64_t l, h;
+    int64_t l = 0, h = 0;
     st = state_range(s, s->q[s->cur], &l, &h);
     if (st != FQNM_OK) return st;
     const size_t W = (size_t)(h - l + 1);
