@@ -460,6 +460,7 @@ def other_workloads(F, torch, stream):
         "density_balance_exact": inv1["mass"][0] == q0[0] - inv1["boundary_flux"][0],
     }
     out["burgers_2d_4096"] = nd_workload(F, torch, stream, (4096, 4096), 240)
+    out["burgers_2d_8192"] = nd_workload(F, torch, stream, (8192, 8192), 48)
     out["burgers_3d_256"] = nd_workload(F, torch, stream, (256, 256, 256), 96)
     out["burgers_sine_convergence"] = convergence_sweep(F, torch, stream)
     out["level_statistics_1m"] = level_statistics(F, torch, stream)
@@ -472,7 +473,8 @@ def nd_workload(F, torch, stream, dims, steps):
     p = I.burgers_nd_problem(dims, steps=steps)
     u0 = torch.from_numpy(p.u0).cuda()
     out = {"dims": list(dims), "n_cells": p.n, "time_steps": steps}
-    plans = [("default", {})] + ([("one_step", {"kernel": 1})] if len(dims) == 2 else [])
+    plans = [("default", {})] + ([("tile_64x32", {"nd_tile": 3}), ("one_step", {"kernel": 1})]
+                                 if len(dims) == 2 else [])
     for name, opt in plans:
         s = F.Solver.for_problem(p, **opt)
         s.set_grid(p.dims)

@@ -144,12 +144,12 @@ typedef enum {
                                 its double in the int64 state slot (load, checkpoint); its
                                 invariants are reported as 0.  Set before loading. */
     FQNM_OPT_ND_TILE = 13    /* 2-D grids, K steps per launch (FQNM_OPT_K, default 4):
-                                register tiles of x by y cells, 1 64x64, 2 128x64, 3 64x32
-                                (0: the default, 3), 4 128x32, 5 32x128 (K below half the
-                                smaller side); 6 warps walking y with the K steps pipelined
-                                (K in 1, 2, 3, 4, 6, 8; others round down).  FQNM_OPT_KERNEL = 1
-                                selects one step per launch.  3-D grids always step once per
-                                launch (blocks of rows walking z). */
+                                0 or 6 (default) warps walking y with the K steps pipelined
+                                (K in 1, 2, 3, 4, 6, 8; others round down); 1..5 register tiles
+                                of x by y cells, 1 64x64, 2 128x64, 3 64x32, 4 128x32, 5 32x128
+                                (K below half the smaller side).  FQNM_OPT_KERNEL = 1 selects one
+                                step per launch.  3-D grids always step once per launch (blocks
+                                of rows walking z). */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 

@@ -880,8 +880,8 @@ static NdPlan nd_plan(const fqnm_solver* s)
 {
     NdPlan p;
     p.blocked = s->grid.d == 2 && s->opt_kernel != 1;
-    p.walk = s->opt_nd_tile == ND_WALK;
-    if (s->opt_nd_tile && !p.walk) p.shape = s->opt_nd_tile;
+    p.walk = s->opt_nd_tile == 0 || s->opt_nd_tile == ND_WALK;
+    if (!p.walk) p.shape = s->opt_nd_tile;
     const int lim = p.walk ? 8 : std::min(nd_tile_x(p.shape), nd_tile_y(p.shape)) / 2 - 1;
     p.k = s->opt_k > 0 ? std::min(s->opt_k, lim) : std::min(4, lim);
     return p;

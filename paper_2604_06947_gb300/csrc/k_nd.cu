@@ -385,16 +385,18 @@ cudaError_t dispatch_2d(const Ev& ev, const NdPlan& p, const int32_t* qin, int32
 
 // ---- 2-D temporal walk ------------------------------------------------------------
 // A warp holds a strip of 64 columns (lane l: columns 2l and 2l+1) and walks
-// y, applying K steps as a pipeline: at input row i, level t+1 produces row
-// i-t-1 from level t's rows i-t-2, i-t-1 (kept in registers) and i-t (just
-// produced).  Inside a lane the two columns see each other directly; across
-// lanes one shuffle per cell.  The strip's two outer columns take ghost
-// copies of themselves, so after K levels columns [K, 64-K) are exact, and
-// rows [y0, y1) are exact once the walk has read rows y0-K .. y1+K-1.  No
-// shared memory and no barrier; row loads are issued WALK_AHEAD rows ahead.
+// y, applying K steps as a skewed pipeline: at tick i, level l produces row
+// i - 2l (level 0: the loaded row i) from level l-1's last three rows
+// i-2l-1, i-2l, i-2l+1, all produced on earlier ticks.  The K levels of a
+// tick are therefore independent of one another (2K independent table
+// gathers per lane per tick), which hides the gather latency inside the
+// warp.  Inside a lane the two columns see each other directly; across lanes
+// one shuffle per cell.  The strip's two outer columns take ghost copies of
+// themselves, so after K levels columns [K, 64-K) are exact, and rows
+// [y0, y1) are exact once the walk has read rows y0-K .. y1+K-1.  No shared
+// memory and no barrier; row loads are issued WALK_AHEAD rows ahead.
 
 constexpr int WALK_COLS = 64;
-
 constexpr int WALK_AHEAD = 4;             // rows loaded ahead of the walk
 
 template <class Ev, int K>
@@ -412,8 +414,9 @@ k_walk2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long
     const long long y0 = chunk * R, y1 = y0 + R < ny ? y0 + R : ny;
     unsigned acc = 0;
 
-    // level windows: center row (q, p, m) and the p of the row below, two columns
-    int qC[K][2], pC[K][2], mC[K][2], pD[K][2];
+    // per level l < K: its last three rows, two columns: up (q, p, m) = the
+    // newest, center (q, p, m), down (p)
+    int qU[K][2], pU[K][2], mU[K][2], qC[K][2], pC[K][2], mC[K][2], pD[K][2];
     {
         const int* row = qin + wrap_index(y0 - K - 1, ny) * nx;
         const int a = __ldg(row + xa), b = __ldg(row + xb);
@@ -421,12 +424,11 @@ k_walk2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long
         ev(a, pa, ma, acc);
         ev(b, pb, mb, acc);
 #pragma unroll
-        for (int t = 0; t < K; ++t) {                   // ghosts: never reach an output
-            qC[t][0] = a; pC[t][0] = pa; mC[t][0] = ma; pD[t][0] = pa;
-            qC[t][1] = b; pC[t][1] = pb; mC[t][1] = mb; pD[t][1] = pb;
+        for (int l = 0; l < K; ++l) {                   // ghosts: never reach an output
+            qU[l][0] = qC[l][0] = a; pU[l][0] = pC[l][0] = pD[l][0] = pa; mU[l][0] = mC[l][0] = ma;
+            qU[l][1] = qC[l][1] = b; pU[l][1] = pC[l][1] = pD[l][1] = pb; mU[l][1] = mC[l][1] = mb;
         }
     }
-    // rows i .. i+WALK_AHEAD-1 in flight
     int fa[WALK_AHEAD], fb[WALK_AHEAD];
 #pragma unroll
     for (int a = 0; a < WALK_AHEAD; ++a) {
@@ -438,8 +440,12 @@ k_walk2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long
     const long long oa = strip * SW + (ca - K), ob = strip * SW + (cb - K);
     const bool wa = ca >= K && ca < WALK_COLS - K && oa < nx;
     const bool wb = cb >= K && cb < WALK_COLS - K && ob < nx;
-    for (long long i = y0 - K; i < y1 + K; ++i) {
-        int nq[2] = {fa[0], fb[0]};
+    // level K row i - 2K lands in [y0, y1) for i in [y0 + 2K, y1 + 2K)
+    for (long long i = y0 - K; i < y1 + 2 * K; ++i) {
+        // new rows of every level this tick, from the windows as they stood
+        int nq[K + 1][2];
+        nq[0][0] = fa[0];
+        nq[0][1] = fb[0];
 #pragma unroll
         for (int a = 0; a + 1 < WALK_AHEAD; ++a) {
             fa[a] = fa[a + 1];
@@ -450,45 +456,49 @@ k_walk2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long
             fa[WALK_AHEAD - 1] = __ldg(row + xa);
             fb[WALK_AHEAD - 1] = __ldg(row + xb);
         }
-        int np[2], nm[2];
-        ev(nq[0], np[0], nm[0], acc);
-        ev(nq[1], np[1], nm[1], acc);
 #pragma unroll
-        for (int t = 0; t < K; ++t) {
-            int pl = __shfl_up_sync(0xffffffffu, pC[t][1], 1);
-            int mr = __shfl_down_sync(0xffffffffu, mC[t][0], 1);
-            if (lane == 0) pl = pC[t][0];               // ghost of the strip's first column
-            if (lane == 31) mr = mC[t][1];              // ghost of the strip's last column
-            const int v0 = qC[t][0] - 2 * (pC[t][0] - mC[t][0]) + pl + pD[t][0] - mC[t][1] - nm[0];
-            const int v1 = qC[t][1] - 2 * (pC[t][1] - mC[t][1]) + pC[t][0] + pD[t][1] - mr - nm[1];
-            pD[t][0] = pC[t][0]; qC[t][0] = nq[0]; pC[t][0] = np[0]; mC[t][0] = nm[0];
-            pD[t][1] = pC[t][1]; qC[t][1] = nq[1]; pC[t][1] = np[1]; mC[t][1] = nm[1];
-            nq[0] = v0;
-            nq[1] = v1;
-            if (t < K - 1) {
-                ev(nq[0], np[0], nm[0], acc);
-                ev(nq[1], np[1], nm[1], acc);
+        for (int l = 0; l < K; ++l) {                   // level l+1 from level l's window
+            int pl = __shfl_up_sync(0xffffffffu, pC[l][1], 1);
+            int mr = __shfl_down_sync(0xffffffffu, mC[l][0], 1);
+            if (lane == 0) pl = pC[l][0];               // ghost of the strip's first column
+            if (lane == 31) mr = mC[l][1];              // ghost of the strip's last column
+            nq[l + 1][0] = qC[l][0] - 2 * (pC[l][0] - mC[l][0]) + pl + pD[l][0] - mC[l][1] - mU[l][0];
+            nq[l + 1][1] = qC[l][1] - 2 * (pC[l][1] - mC[l][1]) + pC[l][0] + pD[l][1] - mr - mU[l][1];
+        }
+        // shift every level's window by its new row (levels 0 .. K-1), evaluating it
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                pD[l][c] = pC[l][c];
+                qC[l][c] = qU[l][c];
+                pC[l][c] = pU[l][c];
+                mC[l][c] = mU[l][c];
+                qU[l][c] = nq[l][c];
+                ev(nq[l][c], pU[l][c], mU[l][c], acc);
             }
         }
-        const long long r = i - K;                      // level-K row
+        const long long r = i - 2 * K;                  // level-K row of this tick
         if (r >= y0 && r < y1) {
-            if (wa) qout[r * nx + oa] = nq[0];
-            if (wb) qout[r * nx + ob] = nq[1];
+            if (wa) qout[r * nx + oa] = nq[K][0];
+            if (wb) qout[r * nx + ob] = nq[K][1];
         }
     }
     if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
 }
 
+// Rows per warp R: enough warps for about 24 per SM (latency hiding),
+// between 4K (the walk re-reads 2K halo rows and fills its pipeline for K
+// more ticks per R rows) and 256.
 template <class Ev, int K>
 cudaError_t launch_walk(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
                         unsigned* err, cudaStream_t st)
 {
     const long long nx = g.dims[0], ny = g.dims[1];
     const long long strips = (nx + (WALK_COLS - 2 * K) - 1) / (WALK_COLS - 2 * K);
-    // rows per warp: enough warps to fill every SM (about 24 each), at most 256
     const long long target = 152LL * 24;
     long long R = (ny * strips + target - 1) / target;
-    R = R < 16 ? 16 : (R > 256 ? 256 : R);
+    R = R < 4 * K ? 4 * K : (R > 256 ? 256 : R);
     const long long chunks = (ny + R - 1) / R;
     const long long blocks = (strips * chunks + 7) / 8;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;

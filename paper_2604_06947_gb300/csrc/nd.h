@@ -23,7 +23,7 @@ enum NdTile { ND_TILE_64x64 = 1, ND_TILE_128x64 = 2, ND_TILE_64x32 = 3, ND_TILE_
               ND_TILE_32x128 = 5, ND_WALK = 6 };
 struct NdPlan {
     int blocked = 0;              // 0: one step per launch (walking kernels)
-    int walk = 0;                 // blocked: 1 pipelined walk along y, 0 register tiles
+    int walk = 1;                 // blocked: 1 pipelined walk along y, 0 register tiles
     int shape = ND_TILE_64x32;
     int k = 4;
 };
