@@ -507,9 +507,10 @@ int orc_fv_step_f32(int kind, double a, double alpha, double dx, double dt,
 /* 1-D Euler, Roe flux (§3.3 "Sod shock tube under Roe flux quantisation").  */
 /* Conserved U = (rho, m, E), p = (gamma-1)(E - m^2/(2 rho)).                */
 /* Textbook Roe flux, no entropy fix (reading R5), evaluated in this order:  */
-/*   uK = mK/rhoK; pK = (g-1)*(EK - 0.5*(rhoK*(uK*uK))); HK = (EK+pK)/rhoK   */
-/*   sL = sqrt(rhoL); sR = sqrt(rhoR); w = sL + sR                           */
-/*   ut = (sL*uL + sR*uR)/w;  Ht = (sL*HL + sR*HR)/w                         */
+/*   iK = 1/rhoK; uK = mK*iK; pK = (g-1)*(EK - 0.5*(rhoK*(uK*uK)));          */
+/*   HK = (EK+pK)*iK                                                         */
+/*   sL = sqrt(rhoL); sR = sqrt(rhoR); w = sL + sR; iw = 1/w                 */
+/*   ut = (sL*uL + sR*uR)*iw;  Ht = (sL*HL + sR*HR)*iw                       */
 /*   ct = sqrt((g-1)*(Ht - 0.5*(ut*ut)))                                     */
 /*   d0 = rhoR-rhoL; d1 = mR-mL; d2 = ER-EL                                  */
 /*   a2 = (g-1)/(ct*ct) * ((d0*(Ht - ut*ut) + ut*d1) - d2)                   */
@@ -524,13 +525,14 @@ void orc_roe_flux(double g, const double* UL, const double* UR, double* F)
 {
     double rhoL = UL[0], mL = UL[1], EL = UL[2];
     double rhoR = UR[0], mR = UR[1], ER = UR[2];
-    double uL = mL / rhoL, uR = mR / rhoR;
+    double iL = 1.0 / rhoL, iR = 1.0 / rhoR;
+    double uL = mL * iL, uR = mR * iR;
     double pL = (g - 1.0) * (EL - 0.5 * (rhoL * (uL * uL)));
     double pR = (g - 1.0) * (ER - 0.5 * (rhoR * (uR * uR)));
-    double HL = (EL + pL) / rhoL, HR = (ER + pR) / rhoR;
-    double sL = sqrt(rhoL), sR = sqrt(rhoR), w = sL + sR;
-    double ut = (sL * uL + sR * uR) / w;
-    double Ht = (sL * HL + sR * HR) / w;
+    double HL = (EL + pL) * iL, HR = (ER + pR) * iR;
+    double sL = sqrt(rhoL), sR = sqrt(rhoR), w = sL + sR, iw = 1.0 / w;
+    double ut = (sL * uL + sR * uR) * iw;
+    double Ht = (sL * HL + sR * HR) * iw;
     double ct = sqrt((g - 1.0) * (Ht - 0.5 * (ut * ut)));
     double d0 = rhoR - rhoL, d1 = mR - mL, d2 = ER - EL;
     double a2 = (g - 1.0) / (ct * ct) * ((d0 * (Ht - ut * ut) + ut * d1) - d2);

@@ -1,9 +1,9 @@
 // roe.cuh -- Roe flux of the 1-D Euler equations on the GPU (§3.3).
 //
 // Textbook Roe flux, no entropy fix, gamma-law gas, conserved U = (rho, m, E):
-//   uK = mK/rhoK, pK = (g-1)*(EK - 0.5*(rhoK*(uK*uK))), HK = (EK+pK)/rhoK
-//   sL = sqrt(rhoL), sR = sqrt(rhoR), w = sL + sR
-//   ut = (sL*uL + sR*uR)/w, Ht = (sL*HL + sR*HR)/w
+//   iK = 1/rhoK, uK = mK*iK, pK = (g-1)*(EK - 0.5*(rhoK*(uK*uK))), HK = (EK+pK)*iK
+//   sL = sqrt(rhoL), sR = sqrt(rhoR), w = sL + sR, iw = 1/w
+//   ut = (sL*uL + sR*uR)*iw, Ht = (sL*HL + sR*HR)*iw
 //   ct = sqrt((g-1)*(Ht - 0.5*(ut*ut)))
 //   jumps d0, d1, d2 of rho, m, E; wave strengths
 //   a2 = (g-1)/(ct*ct) * ((d0*(Ht - ut*ut) + ut*d1) - d2)
@@ -54,9 +54,10 @@ __device__ __forceinline__ RoeCell<T> roe_cell(T g, T rho, T m, T E)
     c.rho = rho;
     c.m = m;
     c.E = E;
-    c.u = A::div(m, rho);
+    const T inv = A::div(T(1), rho);
+    c.u = A::mul(m, inv);
     c.p = A::mul(gm1, A::sub(E, A::mul(half, A::mul(rho, A::mul(c.u, c.u)))));
-    c.H = A::div(A::add(E, c.p), rho);
+    c.H = A::mul(A::add(E, c.p), inv);
     c.s = A::sqrt_(rho);
     return c;
 }
@@ -70,9 +71,9 @@ __device__ __forceinline__ void roe_flux_cells(T g, const RoeCell<T>& L, const R
     const T one = T(1), half = T(0.5), gm1 = A::sub(g, one);
     const T rhoL = L.rho, mL = L.m, EL = L.E, uL = L.u, pL = L.p, HL = L.H, sL = L.s;
     const T rhoR = R.rho, mR = R.m, ER = R.E, uR = R.u, pR = R.p, HR = R.H, sR = R.s;
-    const T w = A::add(sL, sR);
-    const T ut = A::div(A::add(A::mul(sL, uL), A::mul(sR, uR)), w);
-    const T Ht = A::div(A::add(A::mul(sL, HL), A::mul(sR, HR)), w);
+    const T w = A::add(sL, sR), iw = A::div(one, w);
+    const T ut = A::mul(A::add(A::mul(sL, uL), A::mul(sR, uR)), iw);
+    const T Ht = A::mul(A::add(A::mul(sL, HL), A::mul(sR, HR)), iw);
     const T uu = A::mul(ut, ut);
     const T ct = A::sqrt_(A::mul(gm1, A::sub(Ht, A::mul(half, uu))));
     const T d0 = A::sub(rhoR, rhoL), d1 = A::sub(mR, mL), d2 = A::sub(ER, EL);
