@@ -71,6 +71,15 @@ typedef enum {
  *   TABLE          caller-supplied integer maps phi+- (fqnm_create_table):
  *                  the transfer rule as the primitive object (§2.2, scope of
  *                  transfer-operator equivalence)
+ *   BURGERS_GODUNOV  Burgers, the two-point Godunov flux (the exact Riemann
+ *                  flux of u^2/2, eq. transfer_operator_equivalence_definition
+ *                  rounded once per face).  Both Engquist-Osher maps are >= 0
+ *                  and one of them is 0 at every face but a transonic shock,
+ *                  where Godunov takes the larger flux, and x -> R(x dt/dx/delta)
+ *                  is monotone; so Phi(qL, qR) = max(phi+_EO(qL), phi-_EO(qR))
+ *                  exactly, and the solver steps with the EO tables and that
+ *                  max at every face.  1-D only (not on grids, in the batch or
+ *                  in the FV baseline); alpha >= max|u| for the CFL check.
  *   EULER_ROE      1-D Euler, gamma-law gas, Roe flux quantised per
  *                  conserved component (§3.3); nvars = 3                    */
 typedef enum {
@@ -78,6 +87,8 @@ typedef enum {
     FQNM_FLUX_LINEAR_LF = 1,
     FQNM_FLUX_BURGERS_LF = 2,
     FQNM_FLUX_BURGERS_EO = 3,
+    FQNM_FLUX_BURGERS_GODUNOV = 4,
+    FQNM_FLUX_CUSTOM_SPLIT = 5,  /* fqnm_create_custom */
     FQNM_FLUX_TABLE = 8,
     FQNM_FLUX_EULER_ROE = 16
 } fqnm_flux_kind;
@@ -110,6 +121,20 @@ fqnm_status fqnm_create(const fqnm_flux* flux, const double* delta, double dx,
 fqnm_status fqnm_create_table(const int32_t* phi_p, const int32_t* phi_m,
                               int64_t lo, int64_t count, double delta,
                               int boundary, fqnm_solver** out);
+
+/* A custom monotone split f = f+ + f- (f+ nondecreasing, f- nonincreasing)
+ * given as host callbacks of u, evaluated only when the transfer maps are
+ * tabulated (at load, over the states' range plus the margin, and again when
+ * a range escape widens it): phi+-(q) = R((f+-(delta*q) * lambda) * (1/delta))
+ * with lambda = dt/dx, the order of the built-in kinds (eq. flux_table).
+ * alpha >= max|f'| is used for the CFL check alpha*dt/dx <= 1.  The
+ * callbacks must be deterministic; they are called from the calling thread
+ * of fqnm_load_* and fqnm_sync/fqnm_step (recovery).  A map value outside
+ * +-1e9 gives FQNM_ERR_OVERFLOW. */
+typedef double (*fqnm_split_fn)(double u, void* user);
+fqnm_status fqnm_create_custom(fqnm_split_fn fplus, fqnm_split_fn fminus, void* user,
+                               double alpha, double delta, double dx, double dt,
+                               int boundary, int rounding, fqnm_solver** out);
 
 fqnm_status fqnm_destroy(fqnm_solver* s);
 

@@ -131,6 +131,9 @@ struct fqnm_solver {
     double dx = 0, dt = 0, lambda = 0;
     int boundary = FQNM_BC_PERIODIC;
     bool user_table = false;
+    // host callbacks of a custom monotone split, tabulated at load
+    fqnm_split_fn fplus = nullptr, fminus = nullptr;
+    void* fuser = nullptr;
     std::vector<int32_t> user_p, user_m;
     int64_t user_lo = 0;
 
@@ -260,8 +263,9 @@ static fqnm_status check_flux(const fqnm_flux* f, const double* delta, double dx
         *nvars = 1;
         break;
     case FQNM_FLUX_BURGERS_EO:
+    case FQNM_FLUX_BURGERS_GODUNOV:
         if (!(f->alpha > 0))
-            return set_error(FQNM_ERR_ARG, "BURGERS_EO needs alpha = max|u| > 0 for the CFL check");
+            return set_error(FQNM_ERR_ARG, "BURGERS_EO/GODUNOV need alpha = max|u| > 0 for the CFL check");
         nu = f->alpha * lam;
         *nvars = 1;
         break;
@@ -297,6 +301,37 @@ extern "C" fqnm_status fqnm_create(const fqnm_flux* flux, const double* delta,
     s->flux = *flux;
     s->nvars = nvars;
     for (int v = 0; v < nvars; ++v) s->delta[v] = delta[v];
+    s->dx = dx;
+    s->dt = dt;
+    s->lambda = dt / dx;
+    s->boundary = boundary;
+    *out = s;
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_create_custom(fqnm_split_fn fplus, fqnm_split_fn fminus, void* user,
+                                          double alpha, double delta, double dx, double dt,
+                                          int boundary, int rounding, fqnm_solver** out)
+{
+    if (!out) return set_error(FQNM_ERR_ARG, "null out");
+    *out = nullptr;
+    if (!fplus || !fminus) return set_error(FQNM_ERR_ARG, "null callback");
+    // the CFL check of a split with max|f'| <= alpha
+    fqnm_flux f{};
+    f.kind = FQNM_FLUX_BURGERS_LF;
+    f.alpha = alpha;
+    f.rounding = rounding;
+    int nvars = 1;
+    fqnm_status st = check_flux(&f, &delta, dx, dt, boundary, &nvars);
+    if (st != FQNM_OK) return st;
+    fqnm_solver* s = new (std::nothrow) fqnm_solver();
+    if (!s) return set_error(FQNM_ERR_OOM, "host allocation failed");
+    f.kind = FQNM_FLUX_CUSTOM_SPLIT;
+    s->flux = f;
+    s->fplus = fplus;
+    s->fminus = fminus;
+    s->fuser = user;
+    s->delta[0] = delta;
     s->dx = dx;
     s->dt = dt;
     s->lambda = dt / dx;
@@ -449,6 +484,31 @@ static fqnm_status read_check(fqnm_solver* s, const ClosedForm* cf, int64_t lo,
 }
 
 // Tabulate the maps over [lo, hi] and choose the evaluator.
+// eq. flux_table for host callbacks, in the order of the built-in maps:
+// u = delta*q (exact), t = f(u), s = t*lambda, phi = R(s*(1/delta)).
+static fqnm_status tabulate_custom(fqnm_solver* s, int64_t lo, int64_t count)
+{
+    s->user_p.resize((size_t)count);
+    s->user_m.resize((size_t)count);
+    const double inv = 1.0 / s->delta[0];
+    for (int64_t k = 0; k < count; ++k) {
+        const double u = s->delta[0] * (double)(lo + k);
+        double fp = s->fplus(u, s->fuser), fm = s->fminus(u, s->fuser);
+        double vp = (fp * s->lambda) * inv, vm = (fm * s->lambda) * inv;
+        switch (s->flux.rounding) {
+        case FQNM_ROUND_HALF_AWAY: vp = std::round(vp); vm = std::round(vm); break;
+        case FQNM_ROUND_FLOOR: vp = std::floor(vp); vm = std::floor(vm); break;
+        default: vp = std::nearbyint(vp); vm = std::nearbyint(vm); break;
+        }
+        if (!(std::fabs(vp) < 1.0e9) || !(std::fabs(vm) < 1.0e9))
+            return set_error(FQNM_ERR_OVERFLOW, "custom map at q = %lld is %g, %g",
+                             (long long)(lo + k), vp, vm);
+        s->user_p[(size_t)k] = (int32_t)vp;
+        s->user_m[(size_t)k] = (int32_t)vm;
+    }
+    return FQNM_OK;
+}
+
 static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
 {
     const int64_t count = hi - lo + 1;
@@ -471,7 +531,11 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
         s->tab_cap = count;
     }
     CK(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned), s->stream));
-    if (s->user_table) {
+    if (s->fplus) {                 // custom split: eq. flux_table on the host, same order
+        fqnm_status st = tabulate_custom(s, lo, count);
+        if (st != FQNM_OK) return st;
+    }
+    if (s->user_table || s->fplus) {
         int32_t *dp = nullptr, *dm = nullptr;
         CK(cudaMalloc(&dp, count * sizeof(int32_t)));
         CK(cudaMalloc(&dm, count * sizeof(int32_t)));
@@ -484,7 +548,10 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
         cudaFree(dp);
         cudaFree(dm);
     } else {
-        CK(launch_build_split_table(s->flux.kind, s->flux.a, s->flux.alpha, s->delta[0],
+        // Godunov steps with the Engquist-Osher maps (and a max at each face)
+        const int table_kind = s->flux.kind == FQNM_FLUX_BURGERS_GODUNOV ? FQNM_FLUX_BURGERS_EO
+                                                                        : s->flux.kind;
+        CK(launch_build_split_table(table_kind, s->flux.a, s->flux.alpha, s->delta[0],
                                     s->lambda, s->flux.rounding, lo, count, s->tab2,
                                     s->tabp, s->d_err, s->stream));
     }
@@ -513,6 +580,7 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
     r.evaluator = EVAL_TABLE;
     r.has_p = (flags & CERT_P_NONZERO) != 0;
     r.has_m = (flags & CERT_M_NONZERO) != 0;
+    r.face_max = s->flux.kind == FQNM_FLUX_BURGERS_GODUNOV;
 
     fqnm_rule_info info{};
     info.lo = lo;
@@ -1297,6 +1365,8 @@ extern "C" fqnm_status fqnm_set_grid(fqnm_solver* s, int d, const size_t* dims)
     if (s->nvars != 1) return set_error(FQNM_ERR_ARG, "grids are for scalar solvers");
     if (d > 1 && s->boundary != FQNM_BC_PERIODIC)
         return set_error(FQNM_ERR_ARG, "d > 1 grids are periodic");
+    if (d > 1 && s->flux.kind == FQNM_FLUX_BURGERS_GODUNOV)
+        return set_error(FQNM_ERR_ARG, "grids step split fluxes (the Godunov face is 1-D only)");
     NdGrid g{d, {1, 1, 1}};
     long long cells = 1;
     for (int m = 0; m < d && d > 1; ++m) {
@@ -1451,6 +1521,8 @@ extern "C" fqnm_status fqnm_fv_create(const fqnm_flux* flux, double dx, double d
     int nvars = 1;
     fqnm_status st = check_flux(flux, ones, dx, dt, boundary, &nvars);
     if (st != FQNM_OK) return st;
+    if (flux->kind == FQNM_FLUX_BURGERS_GODUNOV)
+        return set_error(FQNM_ERR_ARG, "the FV baseline takes split fluxes (use BURGERS_EO)");
     fqnm_fv* f = new (std::nothrow) fqnm_fv();
     if (!f) return set_error(FQNM_ERR_OOM, "host allocation failed");
     f->flux = *flux;

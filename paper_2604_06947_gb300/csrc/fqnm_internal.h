@@ -47,6 +47,7 @@ struct RuleView {
     uint32_t span;        // entries - 1
     int32_t evaluator;    // Evaluator
     int32_t has_p, has_m;
+    int32_t face_max;     // face transfer max(phi+(qL), phi-(qR)) instead of the sum
     ClosedForm cf;        // valid when evaluator == EVAL_CLOSED_FORM (phi+ only)
 };
 

@@ -65,8 +65,8 @@ __global__ void k_step_naive(RuleView r, const int* __restrict__ qin,
         ev(qin[il], pl, ml);
         ev(qin[i], pc, mc);
         ev(qin[ir], pr, mr);
-        const int Fr = pc + mr;                    // F_{i+1/2}
-        const int Fl = pl + mc;                    // F_{i-1/2}
+        const int Fr = r.face_max ? max(pc, mr) : pc + mr;   // F_{i+1/2}
+        const int Fl = r.face_max ? max(pl, mc) : pl + mc;   // F_{i-1/2}
         qout[i] = qin[i] - (Fr - Fl);
         if (!periodic && bflux) {
             if (i == 0) atomicAdd((unsigned long long*)bflux, (unsigned long long)(-(long long)Fl));
@@ -162,8 +162,15 @@ cudaError_t launch_step_tb(const RuleView& r, const Plan& p, const int32_t* qin,
         EvClosedP ev{r.cf, r.lo, r.span};
         return dispatch_tb(ev, p, qin, qout, n, k, err, st);
     }
-    if (!r.has_m) {
+    if (!r.has_m) {                              // phi- == 0: the max is the sum too
         EvTableP ev{r.tabp, r.lo, r.span};
+        return dispatch_tb(ev, p, qin, qout, n, k, err, st);
+    }
+    if (r.face_max) {
+        tb::EvTablePMMax ev;
+        ev.tab = r.tab2;
+        ev.lo = r.lo;
+        ev.span = r.span;
         return dispatch_tb(ev, p, qin, qout, n, k, err, st);
     }
     if (r.tab16) {

@@ -18,8 +18,11 @@ constexpr unsigned FULL = 0xffffffffu;
 // ---- transfer-map evaluators ------------------------------------------------
 // operator()(q, p, m, acc): p = phi+(q), m = phi-(q); acc tracks max(q - lo)
 // as unsigned, so a state below lo or above hi shows up as acc > span.
+// FACE_MAX: the face transfer is max(phi+(q_L), phi-(q_R)) (the Godunov flux
+// of Burgers from its Engquist-Osher maps) instead of the sum.
 
 struct EvTablePM {                    // both maps from the (phi+, phi-) table
+    static constexpr bool FACE_MAX = false;
     static constexpr bool HAS_M = true;
     const int2* __restrict__ tab;
     int lo;
@@ -37,6 +40,7 @@ struct EvTablePM {                    // both maps from the (phi+, phi-) table
 };
 
 struct EvTablePM16 {                  // both maps packed as int16 halves of one word
+    static constexpr bool FACE_MAX = false;
     static constexpr bool HAS_M = true;
     const int* __restrict__ tab;
     int lo;
@@ -54,6 +58,7 @@ struct EvTablePM16 {                  // both maps packed as int16 halves of one
 };
 
 struct EvTableP {                     // phi- == 0 on the range: phi+ only
+    static constexpr bool FACE_MAX = false;
     static constexpr bool HAS_M = false;
     const int* __restrict__ tab;
     int lo;
@@ -70,6 +75,7 @@ struct EvTableP {                     // phi- == 0 on the range: phi+ only
 };
 
 struct EvClosedP {                    // phi+(q) = R(q num/den), phi- == 0
+    static constexpr bool FACE_MAX = false;
     static constexpr bool HAS_M = false;
     ClosedForm cf;
     int lo;
@@ -81,6 +87,10 @@ struct EvClosedP {                    // phi+(q) = R(q num/den), phi- == 0
         p = cf_eval(q, cf);
         m = 0;
     }
+};
+
+struct EvTablePMMax : EvTablePM {    // Godunov faces from the EO maps
+    static constexpr bool FACE_MAX = true;
 };
 
 // ---- temporal-blocked kernel -----------------------------------------------------
@@ -177,7 +187,7 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
                     const int offm = (lane == 0) ? (j < V - 1 ? m[j + 1] : me) : m[j];
                     int mr = __shfl_sync(FULL, offm, (lane + 1) & 31);
                     if (j == V - 1 && last_owner) mr = m[V - 1];
-                    d += m[j] - mr;
+                    d = Ev::FACE_MAX ? max(pl, m[j]) - max(p[j], mr) : d + m[j] - mr;
                 }
                 q[j] += d;
             }
@@ -195,7 +205,7 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
                 int d = pl - p[j];
                 if (Ev::HAS_M) {
                     const int mr = j < V - 1 ? m[j + 1] : mrV;
-                    d += m[j] - mr;
+                    d = Ev::FACE_MAX ? max(pl, m[j]) - max(p[j], mr) : d + m[j] - mr;
                 }
                 q[j] += d;
             }

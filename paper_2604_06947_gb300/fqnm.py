@@ -24,6 +24,7 @@ STATUS = {0: "FQNM_OK", -1: "FQNM_ERR_ARG", -2: "FQNM_ERR_CFL", -3: "FQNM_ERR_RA
           -4: "FQNM_ERR_OVERFLOW", -5: "FQNM_ERR_OOM", -6: "FQNM_ERR_CUDA",
           -7: "FQNM_ERR_TIMEOUT", -8: "FQNM_ERR_STATE", -9: "FQNM_ERR_BUSY"}
 FLUX = {"linear_upwind": 0, "linear_lf": 1, "burgers_lf": 2, "burgers_eo": 3,
+        "burgers_godunov": 4,
         "table": 8, "euler_roe": 16}
 ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
 BOUNDARY = {"periodic": 0, "transmissive": 1}
@@ -84,6 +85,8 @@ _st = C.c_int
 PROTOTYPES = {
     "fqnm_create": (_st, [C.POINTER(fqnm_flux), C.POINTER(C.c_double), C.c_double,
                           C.c_double, C.c_int, C.POINTER(_vp)]),
+    "fqnm_create_custom": (_st, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.c_int, C.c_int, C.POINTER(_vp)]),
     "fqnm_create_table": (_st, [_vp, _vp, C.c_int64, C.c_int64, C.c_double, C.c_int,
                                 C.POINTER(_vp)]),
     "fqnm_destroy": (_st, [_vp]),
@@ -612,6 +615,21 @@ def fqnm_kernel_launches() -> int:
 # small convenience wrapper (still marshalling only)
 # ---------------------------------------------------------------------------
 
+SPLIT_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
+
+
+def fqnm_create_custom(fplus, fminus, alpha: float, delta: float, dx: float, dt: float,
+                       boundary: str = "periodic", rounding: str = "half_even"):
+    """A solver for a custom monotone split given as Python callables of u.
+    Returns (handle, callbacks); keep the callbacks alive with the handle."""
+    cbs = (SPLIT_FN(lambda u, _: fplus(u)), SPLIT_FN(lambda u, _: fminus(u)))
+    h = _vp()
+    _check(load().fqnm_create_custom(C.cast(cbs[0], _vp), C.cast(cbs[1], _vp), None, alpha,
+                                     delta, dx, dt, BOUNDARY[boundary], ROUNDING[rounding],
+                                     C.byref(h)))
+    return h.value, cbs
+
+
 class Solver:
     """Owns one fqnm_solver handle; methods call the functions above."""
 
@@ -622,6 +640,19 @@ class Solver:
         self.n = 0
         for k, v in options.items():
             fqnm_set_option(self.h, k, v)
+
+    @classmethod
+    def custom(cls, fplus, fminus, alpha: float, delta: float, dx: float, dt: float,
+               boundary: str = "periodic", rounding: str = "half_even", **options):
+        """Solver for host callables f+(u), f-(u) (tabulated at load)."""
+        self = cls.__new__(cls)
+        self.nvars = 1
+        self.h, self._callbacks = fqnm_create_custom(fplus, fminus, alpha, delta, dx, dt,
+                                                     boundary, rounding)
+        self.n = 0
+        for k, v in options.items():
+            fqnm_set_option(self.h, k, v)
+        return self
 
     @classmethod
     def for_problem(cls, p, rounding: str = "half_even", **options):

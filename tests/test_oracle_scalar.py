@@ -393,3 +393,23 @@ def test_invariants_hand_worked(orc):
     assert tuple(orc.invariants(q, np.array([0, 6, 2]))) == (7, 6, 1 + 2 + 0)
     assert tuple(orc.invariants(q, boundary="transmissive")) == (7, 3 + 2, 0)
     assert tuple(orc.invariants(np.array([-5]))) == (-5, 0, 0)
+
+
+def test_godunov_transfer_is_the_max_of_the_eo_maps(orc):
+    """For Burgers both Engquist-Osher maps are >= 0 and one of them is 0 at
+    every face but a transonic shock (q_L > 0 > q_R), where the Godunov flux
+    is the larger of f(u_L) and f(u_R); rounding x -> R(x lambda / delta) is
+    monotone, so the two-point Godunov transfer equals
+    max(phi+_EO(q_L), phi-_EO(q_R)) exactly.  Checked on every pair of a
+    range that crosses zero, for the three roundings."""
+    delta, dx, dt = 2.0 ** -6, 1.0 / 64, 0.45 / 64
+    lo, hi = -70, 70
+    for rounding in ("half_even", "half_away", "floor"):
+        p, m = orc.split_table("burgers_eo", delta, dx, dt, lo, hi - lo + 1, alpha=1.1,
+                               rounding=rounding)
+        assert (p >= 0).all() and (m >= 0).all()
+        for qL in range(lo, hi + 1):
+            for qR in range(lo, hi + 1):
+                g = orc.two_point_phi("burgers_godunov", delta, dx, dt, qL, qR,
+                                      rounding=rounding)
+                assert g == max(p[qL - lo], m[qR - lo]), (qL, qR, rounding)
