@@ -174,7 +174,13 @@ typedef enum {
                                 of x by y cells, 1 64x64, 2 128x64, 3 64x32, 4 128x32, 5 32x128
                                 (K below half the smaller side).  FQNM_OPT_KERNEL = 1 selects one
                                 step per launch.  3-D grids always step once per launch (blocks
-                                of rows walking z). */
+                                of rows walking z). */,
+    FQNM_OPT_VERIFY = 14     /* 1: at each synchronising call, check that every integer
+                                variable's total plus its counted boundary transfer still
+                                equals its value at load (eq. exact_conservation holds for
+                                every step, so a difference means the state was changed
+                                outside the steps); FQNM_ERR_STATE if not.  One reduction per
+                                sync.  Default 0. */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 
@@ -355,6 +361,20 @@ fqnm_status fqnm_set_grid(fqnm_solver* s, int d, const size_t* dims);
 fqnm_status fqnm_hopf_lax(const double* x, size_t nx, const double* y,
                           const double* U0y, size_t ny, double t, double* u,
                           int64_t* idx, int on_device, void* stream);
+
+/* Resume from a checkpoint: load the host states q (as fqnm_load_states),
+ * then set the step counter to `step` and the accumulated boundary transfer
+ * to boundary_flux[nvars] (NULL: zero), so that invariants, checkpoints and
+ * FQNM_OPT_VERIFY continue as in an uninterrupted run.  A run resumed from
+ * (fqnm_checkpoint, fqnm_invariants().boundary_flux) is bit-identical to the
+ * uninterrupted one. */
+fqnm_status fqnm_resume(fqnm_solver* s, const void* q, size_t n_cells, uint64_t step,
+                        const int64_t* boundary_flux);
+
+/* The solver's live device state (int32 [n] or int64 [3][n]) after a
+ * synchronisation; valid until the next step, load or destroy.  Writing to
+ * it bypasses the steps (FQNM_OPT_VERIFY reports a changed total). */
+fqnm_status fqnm_state_device(fqnm_solver* s, void** q, size_t* n_cells);
 
 /* Number of cells and of conserved variables of the loaded state (0 cells
  * before the first load). */

@@ -20,6 +20,8 @@
 // restarts only that problem from its initial state with a wider map.
 #include "tile_step.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -606,7 +608,18 @@ static fqnm_status build_epoch_graph(fqnm_batch* b)
     return FQNM_OK;
 }
 
+static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work);
+
+// One serving epoch inside an NVTX range ("fqnm_batch_epoch").
 static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
+{
+    nvtxRangePushA("fqnm_batch_epoch");
+    const fqnm_status st = run_epoch_body(b, did_work);
+    nvtxRangePop();
+    return st;
+}
+
+static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
 {
     *did_work = false;
     const uint64_t t = now_ns();

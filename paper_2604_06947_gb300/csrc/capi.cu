@@ -10,6 +10,8 @@
 #include "hopf_lax.h"
 #include "nd.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -114,6 +116,12 @@ std::vector<std::pair<uint32_t, uint32_t>> convergents(double c, uint32_t maxden
 
 using namespace fqnm;
 
+// NVTX range for the duration of a call (tools such as ncu --nvtx see it).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 #define CK(call)                                                   \
     do {                                                           \
         cudaError_t e_ = (call);                                   \
@@ -144,6 +152,8 @@ struct fqnm_solver {
     int qmask = 7;                          // Euler: components evolved as integers
     NdGrid grid{1, {0, 1, 1}};              // d > 1: the Cartesian step of Theorem (extension)
     int opt_nd_tile = 0;                    // 2-D tile shape (0: default)
+    int verify = 0;                         // check the conserved totals at each sync
+    long long mass0[3] = {0, 0, 0};         // totals the check expects (plus boundary transfer)
 
     // streams
     cudaStream_t stream = nullptr;
@@ -419,6 +429,9 @@ extern "C" fqnm_status fqnm_set_stream(fqnm_solver* s, void* stream)
     return FQNM_OK;
 }
 
+static fqnm_status sync_and_check(fqnm_solver* s);
+static fqnm_status set_expected_totals(fqnm_solver* s);
+
 extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value)
 {
     if (!s) return set_error(FQNM_ERR_ARG, "null handle");
@@ -448,6 +461,16 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_AUTOTUNE: s->autotune = value != 0; break;
     case FQNM_OPT_GRAPH: s->use_graph = value != 0; break;
     case FQNM_OPT_PACK16: s->pack16 = value != 0; break;
+    case FQNM_OPT_VERIFY: {
+        s->verify = value != 0;
+        if (s->verify && s->loaded) {            // expect the totals as they stand now
+            fqnm_status st = sync_and_check(s);
+            if (st != FQNM_OK) return st;
+            st = set_expected_totals(s);
+            if (st != FQNM_OK) return st;
+        }
+        break;
+    }
     case FQNM_OPT_ND_TILE:
         if (value < 0 || value > ND_WALK) return set_error(FQNM_ERR_ARG, "2-D plan 0..6");
         s->opt_nd_tile = (int)value; break;
@@ -802,6 +825,7 @@ static fqnm_status build_for_state(fqnm_solver* s, const void* q)
 
 static fqnm_status load_common(fqnm_solver* s, const void* q, size_t n, bool device)
 {
+    NvtxRange range("fqnm_load");
     if (!s) return set_error(FQNM_ERR_ARG, "null handle");
     if (!q || n == 0) return set_error(FQNM_ERR_ARG, "null states or n == 0");
     if (n > (size_t)INT32_MAX) return set_error(FQNM_ERR_ARG, "n too large");
@@ -835,6 +859,7 @@ static fqnm_status load_common(fqnm_solver* s, const void* q, size_t n, bool dev
     }
     CK(cudaStreamSynchronize(s->stream));
     s->loaded = true;
+    if (s->verify) return set_expected_totals(s);
     return FQNM_OK;
 }
 
@@ -1048,6 +1073,7 @@ static fqnm_status step_any(fqnm_solver* s, uint64_t k)
 
 extern "C" fqnm_status fqnm_step(fqnm_solver* s, uint64_t k)
 {
+    NvtxRange range("fqnm_step");
     if (!s) return set_error(FQNM_ERR_ARG, "null handle");
     if (!s->loaded) return set_error(FQNM_ERR_STATE, "fqnm_step before fqnm_load_states");
     if (k == 0) return FQNM_OK;
@@ -1056,6 +1082,64 @@ extern "C" fqnm_status fqnm_step(fqnm_solver* s, uint64_t k)
 
 // Wait for the stream; on a range escape rebuild a wider map from the last
 // checkpoint and replay the steps since, so that the result is still exact.
+// The exact conserved totals of every integer variable (eq. exact_conservation)
+// and the boundary transfer accumulated since load; synchronises the stream.
+static fqnm_status current_totals(fqnm_solver* s, long long mass[3], long long bflux[3])
+{
+    CK(cudaMemsetAsync(s->d_acc, 0, 9 * sizeof(long long), s->stream));
+    for (int v = 0; v < s->nvars; ++v) {
+        if (s->nvars == 3) {
+            if (!((s->qmask >> v) & 1)) continue;
+            CK(launch_invariants_i64((const int64_t*)s->q[s->cur] + v * s->n, nullptr,
+                                     (int64_t)s->n, 0, s->d_acc + 3 * v, s->stream));
+        } else if (s->grid.d > 1) {
+            CK(launch_invariants_nd((const int32_t*)s->q[s->cur], nullptr, s->grid, s->d_acc,
+                                    s->stream));
+        } else {
+            CK(launch_invariants_i32((const int32_t*)s->q[s->cur], nullptr, (int64_t)s->n, 0,
+                                     s->d_acc, s->stream));
+        }
+    }
+    CK(cudaMemcpyAsync(s->h_acc, s->d_acc, (ACC_BFLUX + 3) * sizeof(long long),
+                       cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int v = 0; v < 3; ++v) {
+        mass[v] = s->h_acc[3 * v];
+        bflux[v] = s->h_acc[ACC_BFLUX + v];
+    }
+    return FQNM_OK;
+}
+
+// Expect mass + boundary transfer to stay what it is now.
+static fqnm_status set_expected_totals(fqnm_solver* s)
+{
+    long long mass[3], bflux[3];
+    fqnm_status st = current_totals(s, mass, bflux);
+    if (st != FQNM_OK) return st;
+    for (int v = 0; v < 3; ++v) s->mass0[v] = mass[v] + bflux[v];
+    return FQNM_OK;
+}
+
+// FQNM_OPT_VERIFY: every step conserves sum q exactly, so sum q + the
+// transfer through the ends must equal its value at load; a difference
+// means the state changed outside the library (or was corrupted).
+static fqnm_status verify_totals(fqnm_solver* s)
+{
+    long long mass[3], bflux[3];
+    fqnm_status st = current_totals(s, mass, bflux);
+    if (st != FQNM_OK) return st;
+    for (int v = 0; v < s->nvars; ++v) {
+        if (s->nvars == 3 && !((s->qmask >> v) & 1)) continue;
+        if (mass[v] + bflux[v] != s->mass0[v])
+            return set_error(FQNM_ERR_STATE,
+                             "conservation check failed at step %llu: variable %d totals %lld, "
+                             "expected %lld (the state changed outside the steps)",
+                             (unsigned long long)s->step_count, v, mass[v] + bflux[v],
+                             s->mass0[v]);
+    }
+    return FQNM_OK;
+}
+
 static fqnm_status sync_and_check(fqnm_solver* s)
 {
     for (int attempt = 0;; ++attempt) {
@@ -1090,6 +1174,10 @@ static fqnm_status sync_and_check(fqnm_solver* s)
         s->info.recoveries += 1;
         s->step_count = s->ckpt_step;
         st = step_any(s, replay);
+        if (st != FQNM_OK) return st;
+    }
+    if (s->verify) {
+        fqnm_status st = verify_totals(s);
         if (st != FQNM_OK) return st;
     }
     // new checkpoint
@@ -1134,6 +1222,7 @@ extern "C" fqnm_status fqnm_observe_device(fqnm_solver* s, void* u, int fp32)
 
 extern "C" fqnm_status fqnm_observe(fqnm_solver* s, double* u)
 {
+    NvtxRange range("fqnm_observe");
     if (!s || !u) return set_error(FQNM_ERR_ARG, "null argument");
     if (!s->loaded) return set_error(FQNM_ERR_STATE, "not loaded");
     fqnm_status st = sync_and_check(s);
@@ -1232,6 +1321,7 @@ static fqnm_status level_check(fqnm_solver* s)
 
 extern "C" fqnm_status fqnm_level_step(fqnm_solver* s, fqnm_level_stats_t* out)
 {
+    NvtxRange range("fqnm_level_step");
     fqnm_status st = level_check(s);
     if (st != FQNM_OK) return st;
     if (!out) return set_error(FQNM_ERR_ARG, "null output");
@@ -1324,6 +1414,7 @@ extern "C" fqnm_status fqnm_hopf_lax(const double* x, size_t nx, const double* y
                                      const double* U0y, size_t ny, double t, double* u,
                                      int64_t* idx, int on_device, void* stream)
 {
+    NvtxRange range("fqnm_hopf_lax");
     if (!x || !y || !U0y || !u) return set_error(FQNM_ERR_ARG, "null array");
     if (nx == 0 || ny == 0) return set_error(FQNM_ERR_ARG, "empty points or candidates");
     if (nx > (size_t)INT32_MAX * 4 || ny > (size_t)INT64_MAX / 8)
@@ -1388,6 +1479,38 @@ extern "C" fqnm_status fqnm_set_grid(fqnm_solver* s, int d, const size_t* dims)
     if (d == 1) g = NdGrid{1, {0, 1, 1}};
     s->grid = g;
     destroy_graph(s);
+    return FQNM_OK;
+}
+
+// ---- resume and the live state --------------------------------------------------
+
+extern "C" fqnm_status fqnm_resume(fqnm_solver* s, const void* q, size_t n, uint64_t step,
+                                   const int64_t* boundary_flux)
+{
+    fqnm_status st = load_common(s, q, n, false);
+    if (st != FQNM_OK) return st;
+    long long b[3] = {0, 0, 0};
+    for (int v = 0; v < s->nvars && boundary_flux; ++v) b[v] = boundary_flux[v];
+    CK(cudaMemcpyAsync(s->d_acc + ACC_BFLUX, b, 3 * sizeof(long long), cudaMemcpyHostToDevice,
+                       s->stream));
+    CK(cudaMemcpyAsync(s->d_acc + ACC_BFLUX_CKPT, b, 3 * sizeof(long long),
+                       cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int v = 0; v < 3; ++v) s->ckpt_bflux[v] = b[v];
+    s->step_count = step;
+    s->ckpt_step = step;
+    if (s->verify) return set_expected_totals(s);
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_state_device(fqnm_solver* s, void** q, size_t* n_cells)
+{
+    if (!s || !q) return set_error(FQNM_ERR_ARG, "null argument");
+    if (!s->loaded) return set_error(FQNM_ERR_STATE, "not loaded");
+    fqnm_status st = sync_and_check(s);
+    if (st != FQNM_OK) return st;
+    *q = s->q[s->cur];
+    if (n_cells) *n_cells = s->n;
     return FQNM_OK;
 }
 

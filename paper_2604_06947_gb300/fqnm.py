@@ -30,7 +30,7 @@ ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
 BOUNDARY = {"periodic": 0, "transmissive": 1}
 OPTION = {"kernel": 0, "layout": 1, "cells_per_thread": 2, "block": 3, "k": 4,
           "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9,
-          "pdl": 10, "pack16": 11, "quantise_mask": 12, "nd_tile": 13}
+          "pdl": 10, "pack16": 11, "quantise_mask": 12, "nd_tile": 13, "verify": 14}
 
 
 class FqnmError(RuntimeError):
@@ -108,6 +108,8 @@ PROTOTYPES = {
                                       C.POINTER(C.c_int64), _vp]),
     "fqnm_get_size": (_st, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "fqnm_set_grid": (_st, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
+    "fqnm_resume": (_st, [_vp, _vp, C.c_size_t, C.c_uint64, C.POINTER(C.c_int64)]),
+    "fqnm_state_device": (_st, [_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)]),
     "fqnm_hopf_lax": (_st, [_vp, C.c_size_t, _vp, _vp, C.c_size_t, C.c_double, _vp, _vp,
                             C.c_int, _vp]),
     "fqnm_level_step": (_st, [_vp, C.POINTER(fqnm_level_stats_t)]),
@@ -353,6 +355,28 @@ def fqnm_invariants_noalloc(q_dev, n: int, other_dev=None, boundary: str = "peri
     _check(load().fqnm_invariants_noalloc(_dptr(q_dev), _dptr(other_dev) or None, n,
                                           BOUNDARY[boundary], out, _stream(stream)))
     return out[0], out[1], out[2]
+
+
+def fqnm_resume(h: int, q, step: int, boundary_flux=None, nvars: Optional[int] = None):
+    """Load checkpointed states and continue at `step` with the given boundary
+    transfer totals (as returned by fqnm_invariants)."""
+    hv = fqnm_get_size(h)[1]
+    q = np.ascontiguousarray(q, dtype=np.int32 if hv == 1 else np.int64)
+    n = q.shape[-1] if q.ndim > 1 else q.shape[0]
+    if q.size != hv * n:
+        raise ValueError("states must be [%d][n]" % hv)
+    bf = None
+    if boundary_flux is not None:
+        bf = (C.c_int64 * 3)(*[int(v) for v in list(boundary_flux)[:hv]])
+    _check(load().fqnm_resume(h, q.ctypes.data, n, int(step), bf))
+
+
+def fqnm_state_device(h: int):
+    """(device pointer, cells) of the live state."""
+    ptr = _vp()
+    n = C.c_size_t(0)
+    _check(load().fqnm_state_device(h, C.byref(ptr), C.byref(n)))
+    return ptr.value, n.value
 
 
 def fqnm_set_grid(h: int, dims) -> None:
