@@ -68,10 +68,17 @@ def kernel_digest(files=STEP_KERNEL_SOURCES) -> str:
     return _digest([os.path.join(CSRC, f) for f in files])[:16]
 
 
-def _compile(cu: str, verbose: bool) -> str:
+def lib_path(checked: bool = False) -> str:
+    """The library; the checked variant (-DFQNM_CHECKED: computed indices
+    verified before each access, a bad one reported as an error) is a
+    separate file."""
+    return os.path.join(BUILD, "libfqnm_checked.so") if checked else LIB
+
+
+def _compile(cu: str, verbose: bool, checked: bool = False) -> str:
     src = os.path.join(CSRC, cu)
-    obj = os.path.join(BUILD, cu[:-3] + ".o")
-    cmd = [nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj]
+    obj = os.path.join(BUILD, cu[:-3] + (".checked.o" if checked else ".o"))
+    cmd = [nvcc()] + NVCC_FLAGS + (["-DFQNM_CHECKED"] if checked else []) + ["-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -82,29 +89,33 @@ def _compile(cu: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int = 0) -> str:
-    """Compile libfqnm if its sources changed; returns the .so path."""
+def build(force: bool = False, verbose: bool = False, jobs: int = 0,
+          checked: bool = False) -> str:
+    """Compile libfqnm (or its checked variant) if its sources changed;
+    returns the .so path."""
     os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "libfqnm.sha256")
+    out = lib_path(checked)
+    stamp = out[:-3] + ".sha256"
     digest = source_digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(out) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == digest:
-                return LIB
+                return out
     cus, _ = sources()
     jobs = jobs or min(len(cus), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda c: _compile(c, verbose), cus))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+        objs = list(ex.map(lambda c: _compile(c, verbose, checked), cus))
+    tmp = out + ".%d.tmp" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     with open(stamp, "w") as fh:
         fh.write(digest)
-    return LIB
+    return out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

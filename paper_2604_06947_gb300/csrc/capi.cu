@@ -1150,6 +1150,8 @@ static fqnm_status sync_and_check(fqnm_solver* s)
         if (e == 0) break;
         if (e & ERRBIT_OVERFLOW)
             return set_error(FQNM_ERR_OVERFLOW, "a transfer does not fit its integer type");
+        if (e & ERRBIT_BOUNDS)
+            return set_error(FQNM_ERR_STATE, "checked build: a computed index left its buffer");
         if (!(e & ERRBIT_RANGE))
             return set_error(FQNM_ERR_TIMEOUT, "device error word 0x%x", e);
         if (!s->recover || s->nvars != 1 || s->user_table || attempt >= 4)
@@ -1346,6 +1348,8 @@ extern "C" fqnm_status fqnm_level_step(fqnm_solver* s, fqnm_level_stats_t* out)
     CK(level_transition(s->levels, qn, qn1, (int64_t)s->n, lo, W, s->stream));
     unsigned e = 0;
     CK(level_record(s->levels, &s->level_last, &e, s->stream));
+    if (e & ERRBIT_BOUNDS)
+        return set_error(FQNM_ERR_STATE, "checked build: a computed index left its buffer");
     if (e) return set_error(FQNM_ERR_RANGE, "a level left [%lld, %lld]", (long long)lo,
                             (long long)(lo + W - 1));
     s->level_last.step = n0;

@@ -11,6 +11,19 @@
 
 #include "../../include/fqnm.h"
 
+// Checked builds (-DFQNM_CHECKED, the stand-in for a sanitizer): the index
+// computations that are not bounded by construction are verified before the
+// access; a bad one sets ERRBIT_BOUNDS and the access is skipped.  In the
+// normal build the check is `true` and compiles away.
+#ifdef FQNM_CHECKED
+#define FQNM_IN_RANGE(i, n, err)                                                  \
+    ((unsigned long long)(i) < (unsigned long long)(n)                             \
+         ? true                                                                    \
+         : (atomicOr((err), ERRBIT_BOUNDS), false))
+#else
+#define FQNM_IN_RANGE(i, n, err) true
+#endif
+
 namespace fqnm {
 
 // Bits of the per-handle device error word.
@@ -18,6 +31,7 @@ enum : unsigned {
     ERRBIT_RANGE = 1u,      // a state left [lo, hi] of the verified transfer map
     ERRBIT_OVERFLOW = 2u,   // a value does not fit its integer type
     ERRBIT_TIMEOUT = 4u,    // a bounded device wait ran out
+    ERRBIT_BOUNDS = 8u,     // (checked builds) a computed index left its buffer
 };
 
 enum Layout : int { LAYOUT_INTERLEAVED = 1, LAYOUT_BLOCKED = 2 };

@@ -102,7 +102,7 @@ __global__ void k_euler_step(const int64_t* __restrict__ qin,
         Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
         Dl[k] = __shfl_up_sync(0xffffffffu, Dr[k], 1);
     }
-    if (lane < 1 || lane > EULER_OWN || c >= n) return;
+    if (lane < 1 || lane > EULER_OWN || c >= n || !FQNM_IN_RANGE(c, n, err)) return;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if ((P.mask >> k) & 1) {

@@ -379,7 +379,8 @@ k_radix_count(const unsigned long long* __restrict__ keys, long long n, int shif
 
 __global__ void __launch_bounds__(RADIX_THREADS)
 k_radix_scatter(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
-                long long n, int shift, long long ntiles, const unsigned* __restrict__ offsets)
+                long long n, int shift, long long ntiles, const unsigned* __restrict__ offsets,
+                unsigned* __restrict__ err)
 {
     __shared__ unsigned whist[RADIX_WARPS][RADIX_DIGITS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -409,7 +410,8 @@ k_radix_scatter(const unsigned long long* __restrict__ in, unsigned long long* _
         const unsigned long long key = i < n ? in[i] : 0;
         const unsigned d = i < n ? (unsigned)((key >> shift) & (RADIX_DIGITS - 1)) : RADIX_DIGITS;
         const unsigned peers = __match_any_sync(FULLMASK, d);
-        if (d < RADIX_DIGITS) out[whist[w][d] + __popc(peers & lt)] = key;
+        const unsigned long long pos = (unsigned long long)whist[w][d] + __popc(peers & lt);
+        if (d < RADIX_DIGITS && FQNM_IN_RANGE(pos, n, err)) out[pos] = key;
         __syncwarp();
         if (d < RADIX_DIGITS && lane == __ffs(peers) - 1) whist[w][d] += __popc(peers);
         __syncwarp();
@@ -427,11 +429,12 @@ __global__ void k_heads(const unsigned long long* __restrict__ keys, long long n
 
 __global__ void k_compact_heads(const unsigned long long* __restrict__ keys, long long n,
                                 const unsigned* __restrict__ flags, const unsigned* __restrict__ idx,
-                                unsigned long long* __restrict__ head_key, unsigned* __restrict__ head_pos)
+                                unsigned long long* __restrict__ head_key, unsigned* __restrict__ head_pos,
+                                unsigned* __restrict__ err)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        if (flags[i]) {
+        if (flags[i] && FQNM_IN_RANGE(idx[i], n, err)) {
             head_key[idx[i]] = keys[i];
             head_pos[idx[i]] = (unsigned)i;
         }
@@ -631,14 +634,14 @@ cudaError_t level_transition(LevelWork* w, const int32_t* qn, const int32_t* qn1
                                                                   w->counts);
         LCK(scan_u32(w, w->counts, RADIX_DIGITS * ntiles, w->scan, nullptr, st));
         k_radix_scatter<<<(unsigned)ntiles, RADIX_THREADS, 0, st>>>(w->keys[cur], w->keys[1 - cur],
-                                                                    n, shift, ntiles, w->scan);
+                                                                    n, shift, ntiles, w->scan, err);
         launches += 2;
         cur = 1 - cur;
     }
     k_heads<<<g, 256, 0, st>>>(w->keys[cur], n, w->counts);
     LCK(scan_u32(w, w->counts, n, w->scan, w->pairs, st));
     k_compact_heads<<<g, 256, 0, st>>>(w->keys[cur], n, w->counts, w->scan, w->head_key,
-                                       w->head_pos);
+                                       w->head_pos, err);
     // row sums from the entries, then the defect
     k_level_rowacc<<<g, 256, 0, st>>>(w->head_key, w->head_pos, w->pairs, n, uW, w->hist[0],
                                       w->acc, w->acc + W, w->moved);

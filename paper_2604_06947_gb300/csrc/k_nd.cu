@@ -116,7 +116,7 @@ k_march2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, lon
             if (e.need_r) r = g == 0 ? mrc : mr[g - 1];
             const long long v = (long long)q0 - 2LL * ((long long)p0 - (long long)m0) + l + pdn
                                 - (long long)r - (long long)mn[g];
-            if (x < nx && y + g < y1) {
+            if (x < nx && y + g < y1 && FQNM_IN_RANGE((y + g) * nx + x, nx * ny, err)) {
                 if (v < INT_MIN || v > INT_MAX) over = true;
                 qout[(y + g) * nx + x] = (int)v;
             }
@@ -206,7 +206,7 @@ k_march3d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, lon
                 const int pdy = shp[s][w - 1][lane], muy = shm[s][w + 1][lane];
                 const long long v = (long long)q0 - 3LL * ((long long)p0 - (long long)m0) + l + pdy
                                     + pdn - (long long)r - (long long)muy - (long long)mn[g];
-                if (x < nx && z + g < z1) {
+                if (x < nx && z + g < z1 && FQNM_IN_RANGE((z + g) * sz + y * sy + x, nz * sz, err)) {
                     if (v < INT_MIN || v > INT_MAX) over = true;
                     qout[(z + g) * sz + y * sy + x] = (int)v;
                 }
@@ -295,7 +295,10 @@ k_step2d_tb(const int* __restrict__ qin, int* __restrict__ qout, Tile2dArgs a, E
     int q[VY];
 #pragma unroll
     for (int j = 0; j < VY; ++j)
-        q[j] = __ldg(qin + wrap_index(y0 + VY * wy + j, a.ny) * a.nx + gx);
+    {
+        const long long gi = wrap_index(y0 + VY * wy + j, a.ny) * a.nx + gx;
+        q[j] = FQNM_IN_RANGE(gi, a.nx * a.ny, err) ? __ldg(qin + gi) : 0;
+    }
 
     unsigned acc = 0;
     const int wl = wx > 0 ? w - 1 : w, wr = wx < WX - 1 ? w + 1 : w;
@@ -341,7 +344,8 @@ k_step2d_tb(const int* __restrict__ qin, int* __restrict__ qout, Tile2dArgs a, E
                 const int ey = VY * wy + j;
                 if (ey < a.K || ey >= a.K + a.SY) continue;
                 const long long oy = ty * a.SY + (ey - a.K);
-                if (oy < a.ny) qout[oy * a.nx + ox] = q[j];
+                if (oy < a.ny && FQNM_IN_RANGE(oy * a.nx + ox, a.nx * a.ny, err))
+                    qout[oy * a.nx + ox] = q[j];
             }
         }
     }
@@ -480,8 +484,8 @@ k_walk2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long
         }
         const long long r = i - 2 * K;                  // level-K row of this tick
         if (r >= y0 && r < y1) {
-            if (wa) qout[r * nx + oa] = nq[K][0];
-            if (wb) qout[r * nx + ob] = nq[K][1];
+            if (wa && FQNM_IN_RANGE(r * nx + oa, nx * ny, err)) qout[r * nx + oa] = nq[K][0];
+            if (wb && FQNM_IN_RANGE(r * nx + ob, nx * ny, err)) qout[r * nx + ob] = nq[K][1];
         }
     }
     if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);

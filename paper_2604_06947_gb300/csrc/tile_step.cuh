@@ -143,8 +143,10 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
     asm volatile("griddepcontrol.wait;" ::: "memory");
     int q[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j)
-        q[j] = __ldg(qin + wrap_index(start + cell_of<LAYOUT, V>(j), n));
+    for (int j = 0; j < V; ++j) {
+        const long long gi = wrap_index(start + cell_of<LAYOUT, V>(j), n);
+        q[j] = FQNM_IN_RANGE(gi, n, err) ? __ldg(qin + gi) : 0;
+    }
 
     unsigned acc = 0;
     for (int s = 0; s < K; ++s) {
@@ -221,7 +223,7 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
         const long long e = cell_of<LAYOUT, V>(j);
         if (e >= K && e < K + S) {
             const long long o = tile * S + (e - K);
-            if (o < n) qout[o] = q[j];
+            if (o < n && FQNM_IN_RANGE(o, n, err)) qout[o] = q[j];
         }
     }
     if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);

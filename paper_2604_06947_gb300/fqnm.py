@@ -154,8 +154,14 @@ PROTOTYPES = {
 }
 
 
-def lib_path() -> str:
-    return os.path.join(HERE, "_build", "libfqnm.so")
+def lib_path(checked: bool = False) -> str:
+    return os.path.join(HERE, "_build", "libfqnm_checked.so" if checked else "libfqnm.so")
+
+
+def checked_build() -> bool:
+    """FQNM_CHECKED=1 selects the checked library (computed indices verified
+    before each access; a bad one is reported as FQNM_ERR_STATE)."""
+    return os.environ.get("FQNM_CHECKED") == "1"
 
 
 def load(build: bool = True):
@@ -164,10 +170,10 @@ def load(build: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = lib_path()
+        path = lib_path(checked_build())
         if build:
             from . import build as _b
-            path = _b.build()
+            path = _b.build(checked=checked_build())
         if not os.path.exists(path):
             raise FqnmError(-6, "libfqnm is not built (%s); run build()" % path)
         L = C.CDLL(path)
