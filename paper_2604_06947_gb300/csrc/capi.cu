@@ -18,7 +18,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -701,6 +703,52 @@ struct TuneKey {
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, Plan> g_tune_cache;
+static bool g_tune_file_read = false;
+
+// FQNM_TUNE_CACHE=<file>: tuned plans persist across processes, one line per
+// key: "nclass evaluator has_m layout v block k pdl".  Read once (lines that
+// do not parse, or name an unsupported plan, are ignored); rewritten
+// whenever a plan is tuned.  Called with g_tune_mu held.
+static void read_tune_file()
+{
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char* path = std::getenv("FQNM_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    long long nc;
+    int ev, hm, layout, v, block, k, pdl;
+    while (std::fscanf(f, "%lld %d %d %d %d %d %d %d", &nc, &ev, &hm, &layout, &v, &block, &k,
+                       &pdl) == 8) {
+        Plan p;
+        p.kernel = 2;
+        p.layout = layout;
+        p.v = v;
+        p.block = block;
+        p.k = k;
+        p.pdl = pdl != 0;
+        RuleView none{};
+        if (!tb_plan_supported(none, p)) continue;
+        g_tune_cache[TuneKey{nc, ev, hm}] = p;
+    }
+    std::fclose(f);
+}
+
+static void write_tune_file()
+{
+    const char* path = std::getenv("FQNM_TUNE_CACHE");
+    if (!path || !*path) return;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const auto& kv : g_tune_cache)
+        std::fprintf(f, "%lld %d %d %d %d %d %d %d\n", (long long)kv.first.nclass,
+                     kv.first.evaluator, kv.first.has_m, kv.second.layout, kv.second.v,
+                     kv.second.block, kv.second.k, kv.second.pdl ? 1 : 0);
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
 
 static fqnm_status autotune(fqnm_solver* s)
 {
@@ -708,6 +756,7 @@ static fqnm_status autotune(fqnm_solver* s)
     TuneKey key{(int64_t)bit_length((uint64_t)s->n), s->rule.evaluator, s->rule.has_m};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
+        read_tune_file();
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             s->plan = it->second;
@@ -771,6 +820,7 @@ static fqnm_status autotune(fqnm_solver* s)
     s->plan = best;
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune_cache[key] = best;
+    write_tune_file();
     return FQNM_OK;
 }
 
