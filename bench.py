@@ -462,6 +462,7 @@ def other_workloads(F, torch, stream):
     out["burgers_2d_4096"] = nd_workload(F, torch, stream, (4096, 4096), 240)
     out["burgers_2d_8192"] = nd_workload(F, torch, stream, (8192, 8192), 48)
     out["burgers_3d_256"] = nd_workload(F, torch, stream, (256, 256, 256), 96)
+    out["burgers_3d_512"] = nd_workload(F, torch, stream, (512, 512, 512), 24)
     out["burgers_sine_convergence"] = convergence_sweep(F, torch, stream)
     out["level_statistics_1m"] = level_statistics(F, torch, stream)
     return out
@@ -469,12 +470,15 @@ def other_workloads(F, torch, stream):
 
 def nd_workload(F, torch, stream, dims, steps):
     """Burgers on a periodic 2-D or 3-D grid (directional composition):
-    device-timed steps, default plan and (2-D) the one-step kernel."""
+    device-timed steps, the default plan, other K-step plans and the one-step
+    kernel."""
     p = I.burgers_nd_problem(dims, steps=steps)
     u0 = torch.from_numpy(p.u0).cuda()
     out = {"dims": list(dims), "n_cells": p.n, "time_steps": steps}
     plans = [("default", {})] + ([("tile_64x32", {"nd_tile": 3}), ("one_step", {"kernel": 1})]
-                                 if len(dims) == 2 else [])
+                                 if len(dims) == 2 else
+                                 [("walk_k1", {"k": 1}), ("walk_k3", {"k": 3}),
+                                  ("one_step", {"kernel": 1})])
     for name, opt in plans:
         s = F.Solver.for_problem(p, **opt)
         s.set_grid(p.dims)

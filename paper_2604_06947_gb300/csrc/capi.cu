@@ -1017,38 +1017,45 @@ static bool graph_valid(const fqnm_solver* s)
            a.cf.rounding == b.cf.rounding;
 }
 
-// The 2-D plan: temporal-blocked tiles unless the one-step kernel was asked
-// for (FQNM_OPT_KERNEL = 1) or the grid is 3-D.
+// The d-D plan: K steps per launch (the walk, or on 2-D grids register tiles)
+// unless the one-step kernel was asked for (FQNM_OPT_KERNEL = 1).
 static NdPlan nd_plan(const fqnm_solver* s)
 {
     NdPlan p;
-    p.blocked = s->grid.d == 2 && s->opt_kernel != 1;
-    p.walk = s->opt_nd_tile == 0 || s->opt_nd_tile == ND_WALK;
+    p.blocked = s->opt_kernel != 1;
+    p.walk = s->grid.d == 3 || s->opt_nd_tile == 0 || s->opt_nd_tile == ND_WALK;
     if (!p.walk) p.shape = s->opt_nd_tile;
-    const int lim = p.walk ? 8 : std::min(nd_tile_x(p.shape), nd_tile_y(p.shape)) / 2 - 1;
-    p.k = s->opt_k > 0 ? std::min(s->opt_k, lim) : std::min(4, lim);
+    const int lim = s->grid.d == 3 ? 4
+                    : p.walk ? 8 : std::min(nd_tile_x(p.shape), nd_tile_y(p.shape)) / 2 - 1;
+    const int dflt = s->grid.d == 3 ? 2 : 4;      // 3-D: K = 2 keeps 32-row blocks
+    p.k = s->opt_k > 0 ? std::min(s->opt_k, lim) : std::min(dflt, lim);
     return p;
 }
 
-// The walk supports K in {1, 2, 3, 4, 6, 8}: the largest of them <= k.
-static int walk_k(int k)
+// The 2-D walk supports K in {1, 2, 3, 4, 6, 8}, the 3-D walk 1 .. 4: the
+// largest of them <= k.
+static int walk_k(int d, int k)
 {
-    while (k > 1 && !walk_k_supported(k)) --k;
+    while (k > 1 && !(d == 3 ? walk3_k_supported(k) : walk_k_supported(k))) --k;
     return k;
 }
 
 static fqnm_status step_scalar(fqnm_solver* s, uint64_t k)
 {
     if (s->grid.d > 1) {
-        // 2-D: K steps per launch in register tiles (unless the one-step
-        // kernel is asked for); 3-D: one step per launch
+        // K steps per launch by the walk (or 2-D register tiles) unless the
+        // one-step kernel is asked for
         const NdPlan np = nd_plan(s);
         uint64_t done = 0;
         while (done < k) {
             if (np.blocked && np.walk) {
-                const int kk = walk_k((int)std::min<uint64_t>((uint64_t)np.k, k - done));
-                CK(launch_walk2d(s->rule, (const int32_t*)s->q[s->cur], (int32_t*)s->q[1 - s->cur],
-                                 s->grid, kk, s->d_err, s->stream));
+                const int kk = walk_k(s->grid.d, (int)std::min<uint64_t>((uint64_t)np.k, k - done));
+                if (s->grid.d == 3)
+                    CK(launch_walk3d(s->rule, (const int32_t*)s->q[s->cur],
+                                     (int32_t*)s->q[1 - s->cur], s->grid, kk, s->d_err, s->stream));
+                else
+                    CK(launch_walk2d(s->rule, (const int32_t*)s->q[s->cur],
+                                     (int32_t*)s->q[1 - s->cur], s->grid, kk, s->d_err, s->stream));
                 done += kk;
             } else if (np.blocked) {
                 const int kk = (int)std::min<uint64_t>((uint64_t)np.k, k - done);

@@ -526,6 +526,184 @@ cudaError_t dispatch_walk(const Ev& ev, int K, const int32_t* qin, int32_t* qout
     }
 }
 
+// ---- 3-D temporal walk ------------------------------------------------------------
+// A block of ROWS warps holds a 64-column x strip (two columns per lane) of
+// ROWS consecutive y rows (one per warp) and walks z with K
+// steps in the skewed pipeline of the 2-D walk: at tick i level l produces
+// slice i - 2l from level l-1's slices i-2l-1 .. i-2l+1 (z neighbours in
+// registers), x neighbours within the warp, y neighbours from the warps
+// above and below through shared memory.  The levels of a tick are
+// independent, so one barrier per tick serves all of them (double-buffered
+// by tick parity).  Outer columns and the block's first and last rows take
+// ghost copies of themselves: columns [K, 64-K) and rows [K, ROWS-K) are
+// exact after K levels.  ROWS = 32 (1024 threads, at most 64 registers)
+// for K <= 2, where the y halo then costs 1/7 instead of 1/3.
+
+template <int K, int ROWS>
+struct Walk3Smem {
+    int p[2][K][ROWS][WALK_COLS];         // level l's centre slice: p
+    int m[2][K][ROWS][WALK_COLS];         // and m
+};
+
+template <class Ev, int K, int ROWS>
+__global__ void __launch_bounds__(32 * ROWS)
+k_walk3d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long long ny,
+         long long nz, long long strips, long long rowblocks, long long chunks, long long R, Ev ev,
+         unsigned* __restrict__ err)
+{
+    constexpr int SW = WALK_COLS - 2 * K, SR = ROWS - 2 * K;
+    extern __shared__ __align__(16) unsigned char walk3_raw[];
+    Walk3Smem<K, ROWS>& sm = *reinterpret_cast<Walk3Smem<K, ROWS>*>(walk3_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long b = blockIdx.x;
+    const long long strip = b % strips, rb = (b / strips) % rowblocks, chunk = b / (strips * rowblocks);
+    const long long xs = strip * SW - K;
+    const long long xa = wrap_index(xs + 2 * lane, nx), xb = wrap_index(xs + 2 * lane + 1, nx);
+    const long long yr = rb * SR - K + w;                 // this warp's row (unwrapped)
+    const long long y = wrap_index(yr, ny);
+    const long long sy = nx, sz = nx * ny;
+    const long long z0 = chunk * R, z1 = z0 + R < nz ? z0 + R : nz;
+    const int wd = w > 0 ? w - 1 : w, wu = w < ROWS - 1 ? w + 1 : w;
+    unsigned acc = 0;
+
+    int qU[K][2], pU[K][2], mU[K][2], qC[K][2], pC[K][2], mC[K][2], pD[K][2];
+    {
+        const int* row = qin + wrap_index(z0 - K - 1, nz) * sz + y * sy;
+        const int a = __ldg(row + xa), c = __ldg(row + xb);
+        int pa, ma, pc, mc;
+        ev(a, pa, ma, acc);
+        ev(c, pc, mc, acc);
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+            qU[l][0] = qC[l][0] = a; pU[l][0] = pC[l][0] = pD[l][0] = pa; mU[l][0] = mC[l][0] = ma;
+            qU[l][1] = qC[l][1] = c; pU[l][1] = pC[l][1] = pD[l][1] = pc; mU[l][1] = mC[l][1] = mc;
+        }
+    }
+    int fa[WALK_AHEAD], fb[WALK_AHEAD];
+#pragma unroll
+    for (int a = 0; a < WALK_AHEAD; ++a) {
+        const int* row = qin + wrap_index(z0 - K + a, nz) * sz + y * sy;
+        fa[a] = __ldg(row + xa);
+        fb[a] = __ldg(row + xb);
+    }
+    const int ca = 2 * lane, cb = 2 * lane + 1;
+    const long long oa = strip * SW + (ca - K), ob = strip * SW + (cb - K);
+    const bool rowok = w >= K && w < ROWS - K && yr < ny && yr >= 0;
+    const bool wa = rowok && ca >= K && ca < WALK_COLS - K && oa < nx;
+    const bool wb = rowok && cb >= K && cb < WALK_COLS - K && ob < nx;
+    int par = 0;
+    for (long long i = z0 - K; i < z1 + 2 * K; ++i, par ^= 1) {
+        int nq[K + 1][2];
+        nq[0][0] = fa[0];
+        nq[0][1] = fb[0];
+#pragma unroll
+        for (int a = 0; a + 1 < WALK_AHEAD; ++a) {
+            fa[a] = fa[a + 1];
+            fb[a] = fb[a + 1];
+        }
+        {
+            const int* row = qin + wrap_index(i + WALK_AHEAD, nz) * sz + y * sy;
+            fa[WALK_AHEAD - 1] = __ldg(row + xa);
+            fb[WALK_AHEAD - 1] = __ldg(row + xb);
+        }
+        // publish every level's centre slice for the rows above and below
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+            sm.p[par][l][w][ca] = pC[l][0];
+            sm.p[par][l][w][cb] = pC[l][1];
+            sm.m[par][l][w][ca] = mC[l][0];
+            sm.m[par][l][w][cb] = mC[l][1];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < K; ++l) {                   // level l+1 from level l's window
+            int pl = __shfl_up_sync(0xffffffffu, pC[l][1], 1);
+            int mr = __shfl_down_sync(0xffffffffu, mC[l][0], 1);
+            if (lane == 0) pl = pC[l][0];
+            if (lane == 31) mr = mC[l][1];
+            const int pya = sm.p[par][l][wd][ca], pyb = sm.p[par][l][wd][cb];   // row below
+            const int mya = sm.m[par][l][wu][ca], myb = sm.m[par][l][wu][cb];   // row above
+            nq[l + 1][0] = qC[l][0] - 3 * (pC[l][0] - mC[l][0]) + pl + pya + pD[l][0]
+                           - mC[l][1] - mya - mU[l][0];
+            nq[l + 1][1] = qC[l][1] - 3 * (pC[l][1] - mC[l][1]) + pC[l][0] + pyb + pD[l][1]
+                           - mr - myb - mU[l][1];
+        }
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                pD[l][c] = pC[l][c];
+                qC[l][c] = qU[l][c];
+                pC[l][c] = pU[l][c];
+                mC[l][c] = mU[l][c];
+                qU[l][c] = nq[l][c];
+                ev(nq[l][c], pU[l][c], mU[l][c], acc);
+            }
+        }
+        const long long r = i - 2 * K;                  // level-K slice of this tick
+        if (r >= z0 && r < z1) {
+            const long long base = r * sz + y * sy;
+            if (wa && FQNM_IN_RANGE(base + oa, nz * sz, err)) qout[base + oa] = nq[K][0];
+            if (wb && FQNM_IN_RANGE(base + ob, nz * sz, err)) qout[base + ob] = nq[K][1];
+        }
+    }
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+}
+
+template <class Ev, int K, int ROWS>
+cudaError_t launch_walk3(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                         unsigned* err, cudaStream_t st)
+{
+    const long long nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    const long long strips = (nx + (WALK_COLS - 2 * K) - 1) / (WALK_COLS - 2 * K);
+    const long long rowblocks = (ny + (ROWS - 2 * K) - 1) / (ROWS - 2 * K);
+    // One block fills an SM (registers), so blocks run in waves of one per
+    // SM and a block of R slices takes R + 3K ticks: take the chunk count
+    // whose waves x ticks is least.
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 152;
+    }
+    const long long xy = strips * rowblocks;
+    long long R = nz, best = -1;
+    for (long long c = 1; c <= nz && c <= 256; ++c) {
+        const long long r = (nz + c - 1) / c, chunks = (nz + r - 1) / r;
+        const long long cost = ((xy * chunks + sms - 1) / sms) * (r + 3 * K);
+        if (best < 0 || cost < best) { best = cost; R = r; }
+    }
+    const long long chunks = (nz + R - 1) / R;
+    const long long blocks = strips * rowblocks * chunks;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    constexpr int smem = (int)sizeof(Walk3Smem<K, ROWS>);
+    static bool attr_set = false;                 // opt in above the 48 KB default once
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_walk3d<Ev, K, ROWS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_walk3d<Ev, K, ROWS><<<(unsigned)blocks, 32 * ROWS, smem, st>>>(qin, qout, nx, ny, nz, strips,
+                                                                     rowblocks, chunks, R, ev, err);
+    note_launches();
+    return cudaGetLastError();
+}
+
+template <class Ev>
+cudaError_t dispatch_walk3(const Ev& ev, int K, const int32_t* qin, int32_t* qout,
+                           const NdGrid& g, unsigned* err, cudaStream_t st)
+{
+    switch (K) {
+    case 1: return launch_walk3<Ev, 1, 32>(ev, qin, qout, g, err, st);
+    case 2: return launch_walk3<Ev, 2, 32>(ev, qin, qout, g, err, st);
+    case 3: return launch_walk3<Ev, 3, 16>(ev, qin, qout, g, err, st);
+    case 4: return launch_walk3<Ev, 4, 16>(ev, qin, qout, g, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 constexpr int IBLOCK = 256;
 
 __device__ __forceinline__ long long warp_sum64(long long v)
@@ -638,6 +816,19 @@ cudaError_t launch_walk2d(const RuleView& r, const int32_t* qin, int32_t* qout, 
     if (!r.has_m) return dispatch_walk(EvTableP{r.tabp, r.lo, r.span}, K, qin, qout, g, err, st);
     if (r.tab16) return dispatch_walk(EvTablePM16{r.tab16, r.lo, r.span}, K, qin, qout, g, err, st);
     return dispatch_walk(EvTablePM{r.tab2, r.lo, r.span}, K, qin, qout, g, err, st);
+}
+
+bool walk3_k_supported(int K) { return K >= 1 && K <= 4; }
+
+cudaError_t launch_walk3d(const RuleView& r, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                          int K, unsigned* err, cudaStream_t st)
+{
+    if (g.d != 3 || !walk3_k_supported(K)) return cudaErrorInvalidValue;
+    if (r.evaluator == EVAL_CLOSED_FORM && !r.has_m)
+        return dispatch_walk3(EvClosedP{r.cf, r.lo, r.span}, K, qin, qout, g, err, st);
+    if (!r.has_m) return dispatch_walk3(EvTableP{r.tabp, r.lo, r.span}, K, qin, qout, g, err, st);
+    if (r.tab16) return dispatch_walk3(EvTablePM16{r.tab16, r.lo, r.span}, K, qin, qout, g, err, st);
+    return dispatch_walk3(EvTablePM{r.tab2, r.lo, r.span}, K, qin, qout, g, err, st);
 }
 
 cudaError_t launch_invariants_nd(const int32_t* q, const int32_t* other, const NdGrid& gr,

@@ -41,6 +41,12 @@ bool walk_k_supported(int K);
 cudaError_t launch_walk2d(const RuleView& r, const int32_t* qin, int32_t* qout, const NdGrid& g,
                           int K, unsigned* err, cudaStream_t st);
 
+// K steps of eq. nd_transfer_rule on a 3-D grid in one launch by a pipelined
+// walk along z (K in 1 .. 4).
+bool walk3_k_supported(int K);
+cudaError_t launch_walk3d(const RuleView& r, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                          int K, unsigned* err, cudaStream_t st);
+
 // mass, TV summed over the axes (periodic faces), l1 to other (may be null),
 // added to acc[0..2].
 cudaError_t launch_invariants_nd(const int32_t* q, const int32_t* other, const NdGrid& g,

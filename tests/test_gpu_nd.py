@@ -71,6 +71,59 @@ def test_one_step_marching_kernel(orc, dims):
     s.close()
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 7])
+def test_3d_walk_bit_exact(orc, k):
+    """The pipelined 3-D walk (blocks of 16 rows x 64 columns walking z, K
+    levels per launch; 7 is taken as 4 + 3) on ragged grids, grids smaller
+    than one block in x and y, a single slice and a single row."""
+    for dims in ((70, 21, 40), (24, 20, 18), (5, 3, 31), (130, 1, 9), (1, 1, 12), (33, 40, 1)):
+        p = I.burgers_nd_problem(dims)
+        shape = dims[::-1]
+        q0 = orc.quantise(p.u0, p.delta).reshape(shape)
+        s = solver_for(p, k=k).load(q0.reshape(-1))
+        s.step(11)
+        want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 11, alpha=p.alpha)
+        assert np.array_equal(s.state().reshape(shape), want), dims
+        s.close()
+
+
+@pytest.mark.parametrize("opt", [{}, {"pack16": 1}])
+def test_3d_walk_evaluators(orc, opt):
+    """The 3-D walk with the verified closed form (upwind, nu = 0.3 per axis)
+    and with the table evaluators (Lax-Friedrichs split, 16-bit pack)."""
+    dims = (48, 36, 30)
+    shape = dims[::-1]
+    p = I.burgers_nd_problem(dims)
+    q0 = orc.quantise(p.u0, p.delta).reshape(shape)
+    s = solver_for(p, **opt).load(q0.reshape(-1))
+    s.step(13)
+    want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 13, alpha=p.alpha)
+    assert np.array_equal(s.state().reshape(shape), want)
+    s.close()
+    p.flux, p.a, p.alpha = "linear_upwind", 1.0, 0.0
+    p.dt = 0.3 * p.dx
+    s = solver_for(p, **opt).load(q0.reshape(-1))
+    s.step(13)
+    want = orc.step_nd(q0, "linear_upwind", p.delta, p.dx, p.dt, 13, a=1.0)
+    assert np.array_equal(s.state().reshape(shape), want)
+    s.close()
+
+
+def test_full_size_3d_grid(orc):
+    """160^3 cells, 16 steps (four launches of the walk), against the oracle;
+    exact mass."""
+    dims = (160, 160, 160)
+    shape = dims[::-1]
+    p = I.burgers_nd_problem(dims)
+    q0 = orc.quantise(p.u0, p.delta).reshape(shape)
+    s = solver_for(p).load(q0.reshape(-1))
+    s.step(16)
+    want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 16, alpha=p.alpha)
+    assert np.array_equal(s.state().reshape(shape), want)
+    assert s.invariants()["mass"][0] == int(q0.sum())
+    s.close()
+
+
 def test_linear_upwind_closed_form_2d(orc):
     """Upwind a = 1 at nu = 0.45 per axis (d nu = 0.9): phi+ = R(9 q / 20),
     the verified closed form replaces the table."""
