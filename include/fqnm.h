@@ -173,8 +173,9 @@ typedef enum {
                                 (K in 1, 2, 3, 4, 6, 8; others round down); 1..5 register tiles
                                 of x by y cells, 1 64x64, 2 128x64, 3 64x32, 4 128x32, 5 32x128
                                 (K below half the smaller side).  FQNM_OPT_KERNEL = 1 selects one
-                                step per launch.  3-D grids always step once per launch (blocks
-                                of rows walking z). */,
+                                step per launch.  3-D grids take K steps per launch (K in 1..4,
+                                default 2) by blocks of rows walking z; FQNM_OPT_KERNEL = 1
+                                selects one step per launch there too. */,
     FQNM_OPT_VERIFY = 14     /* 1: at each synchronising call, check that every integer
                                 variable's total plus its counted boundary transfer still
                                 equals its value at load (eq. exact_conservation holds for
