@@ -303,6 +303,8 @@ def run_gpu(args):
         if baselines:
             result["fv_baseline"] = baselines
         if serving:
+            if world == 1 and not args.no_cpu:
+                serving["cpu_baseline"] = serving_cpu_baseline()
             result["serving"] = serving
         if workloads:
             result["workloads"] = workloads
@@ -332,34 +334,51 @@ def issue_roofline(counters: dict, launch_s: float, clk: dict):
 
 
 def fv_baselines(F, p, stream, torch):
-    """FP32 / FP64 finite-volume baseline with the same split flux on the same
-    GPU (one step per launch), its throughput and its L1 distance to FQNM."""
-    steps = 2000
+    """FP32 / FP64 finite-volume baselines with the same split flux on the same
+    GPU, one step per launch, and FP32 with 64 steps per launch (the integer
+    kernel's temporal blocking applied to the FP scheme: the ablation that
+    separates the execution strategy from the arithmetic).  Each is
+    device-timed over the workload's steps, and its L1 distance to FQNM is
+    taken at every checkpoint (untimed)."""
+    steps, every = p.steps, 1000
     n = p.n
     q0 = F.fqnm_quantise(p.u0, p.delta)
     u0 = p.delta * q0.astype(np.float64)
-    s = F.Solver.for_problem(p, autotune=1)
-    s.load(q0).step(steps)
-    u_int = s.observe()
+    s = F.Solver.for_problem(p)
+    s.load(q0)
+    ref = []
+    for _ in range(steps // every):
+        s.step(every)
+        ref.append(s.observe())
     s.close()
-    out = {"time_steps": steps}
-    for prec in (32, 64):
+    out = {"time_steps": steps, "checkpoint_every": every}
+    finals = {}
+    for name, prec, K in (("fp32", 32, 1), ("fp64", 64, 1), ("fp32_k64", 32, 64)):
         h = F.fqnm_fv_create(F.make_flux(p.flux, alpha=p.alpha), p.dx, p.dt, "periodic", prec)
         F.fqnm_fv_set_stream(h, stream)
+        F.fqnm_fv_set_k(h, K)
         F.fqnm_fv_load(h, u0)
-        F.fqnm_fv_step(h, 50)
+        F.fqnm_fv_step(h, 64)
         stream.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         F.fqnm_fv_load(h, u0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         F.fqnm_fv_step(h, steps)
         b.record(stream)
         b.synchronize()
         ms = a.elapsed_time(b)
-        u = F.fqnm_fv_observe(h, n)
+        F.fqnm_fv_load(h, u0)
+        l1 = []
+        for c in range(steps // every):
+            F.fqnm_fv_step(h, every)
+            u = F.fqnm_fv_observe(h, n)
+            l1.append(float(p.dx * np.abs(u - ref[c]).sum()))
+        finals[name] = u
         F.fqnm_fv_destroy(h)
-        out["fp%d" % prec] = {"value": n * steps / (ms / 1e3), "unit": UNIT,
-                              "l1_vs_fqnm": float(p.dx * np.abs(u - u_int).sum())}
+        out[name] = {"value": n * steps / (ms / 1e3), "unit": UNIT, "steps_per_launch": K,
+                     "l1_vs_fqnm": l1}
+    out["fp32_k64"]["bitwise_equal_to_fp32"] = bool(np.array_equal(finals["fp32_k64"],
+                                                                   finals["fp32"]))
     return out
 
 
@@ -600,6 +619,22 @@ def serving_block(torch):
 # CPU oracle
 # ---------------------------------------------------------------------------
 
+def host_cpu() -> dict:
+    """The host's CPU model and core count, as the OS reports them."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"cpu_model": model or platform.processor() or "unknown",
+            "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_baseline(p, steps: int = CPU_SAMPLE_STEPS):
     from oracle import oracle as O
     q0 = O.quantise(p.u0, p.delta)
@@ -608,7 +643,38 @@ def cpu_baseline(p, steps: int = CPU_SAMPLE_STEPS):
     dt = time.perf_counter() - t0
     return {"value": p.n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d cells x %d of the 10^4 time steps (same seeded problem), "
-                      "single-threaded C oracle, %.1f s" % (p.n, steps, dt)}
+                      "single-threaded C oracle, %.1f s" % (p.n, steps, dt),
+            "host": host_cpu()}
+
+
+def _oracle_request(rq):
+    """One serving request solved by the single-threaded oracle (a pool
+    worker): returns its cell updates and the seconds of its steps."""
+    from oracle import oracle as O
+    p = I.materialise(rq)
+    q0 = O.quantise(p.u0, p.delta)
+    t0 = time.perf_counter()
+    O.step(q0, p.flux, p.delta, p.dx, p.dt, p.steps, a=p.a, alpha=p.alpha)
+    return p.n * p.steps, time.perf_counter() - t0
+
+
+def serving_cpu_baseline(every: int = 16):
+    """The serving stream's problems on the host cores: one single-threaded
+    oracle instance per core (a spawned process pool), on every 16th request
+    of the 4096; value = their cell updates / the pool's wall time."""
+    import multiprocessing as mp
+    reqs = I.serving_stream()[::every]
+    cores = os.cpu_count() or 1
+    order = sorted(reqs, key=lambda r: -r.problem.n * r.problem.steps)   # longest first
+    with mp.get_context("spawn").Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_request, order, chunksize=1)
+        wall = time.perf_counter() - t0
+    updates = sum(r[0] for r in res)
+    return {"value": updates / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "every %dth request (%d of 4096, %.3g cell updates), one single-threaded "
+                      "C oracle per core, %.1f s wall, %.1f core-s"
+                      % (every, len(reqs), updates, wall, sum(r[1] for r in res))}
 
 
 def run_reference(args):

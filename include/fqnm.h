@@ -416,7 +416,8 @@ fqnm_status fqnm_get_stats(fqnm_solver* s, fqnm_stats* out, int reset);
  * classical_operator_definition, u_i <- u_i - dt/dx (F(u_i,u_{i+1}) -
  * F(u_{i-1},u_i)), F(uL,uR) = f+(uL) + f-(uR), with the same flux as the
  * integer solver, in float (precision 32) or double (64), one step per
- * launch, no FMA contraction.  EULER_ROE runs the Roe flux on [3][n]. */
+ * launch (or K, fqnm_fv_set_k), no FMA contraction.  EULER_ROE runs the Roe
+ * flux on [3][n]. */
 typedef struct fqnm_fv fqnm_fv;
 fqnm_status fqnm_fv_create(const fqnm_flux* flux, double dx, double dt,
                            int boundary, int precision, fqnm_fv** out);
@@ -426,6 +427,12 @@ fqnm_status fqnm_fv_set_stream(fqnm_fv* f, void* stream);
 fqnm_status fqnm_fv_load(fqnm_fv* f, const double* u, size_t n_cells);
 fqnm_status fqnm_fv_load_device(fqnm_fv* f, const double* u, size_t n_cells);
 fqnm_status fqnm_fv_step(fqnm_fv* f, uint64_t k);
+/* Time steps per launch of a periodic scalar baseline, 1..64 (default 1):
+ * K > 1 runs the steps in tiles with a K-cell halo, the temporal blocking of
+ * the integer kernel (an execution strategy: results are bit-identical to
+ * K = 1).  FQNM_ERR_ARG for K outside 1..64, or K > 1 on a transmissive or
+ * Euler baseline. */
+fqnm_status fqnm_fv_set_k(fqnm_fv* f, int k);
 fqnm_status fqnm_fv_observe(fqnm_fv* f, double* u_out);          /* host, syncs */
 fqnm_status fqnm_fv_observe_device(fqnm_fv* f, double* u_out);   /* device */
 fqnm_status fqnm_fv_launches(fqnm_fv* f, uint64_t* launches);
@@ -460,8 +467,10 @@ fqnm_status fqnm_batch_destroy(fqnm_batch* b);
 fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
                                 int k, int layout);
 /* Autotune the plan online: the next epochs with work try each candidate
- * (cells per thread 8/16, 128/256 threads, K 32/64/128) for epochs_per_plan
- * epochs, then keep the one with the least GPU time per cell update. */
+ * (cells per thread 8/16, 32/128/256 threads, K 32/64/128, halo work at most
+ * half the tile) for epochs_per_plan epochs, then keep the one with the
+ * least epoch wall time per cell update (the host's admission, graph replay
+ * and synchronisation included, a fixed cost per epoch). */
 fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan);
 /* The current plan; *tuning = 1 while candidates are still being tried. */
 fqnm_status fqnm_batch_get_plan(fqnm_batch* b, int* cells_per_thread, int* block,

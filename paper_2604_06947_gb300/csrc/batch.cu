@@ -203,10 +203,13 @@ struct fqnm_batch {
     Plan plan;
     int grid = 0;
     cudaGraphExec_t gexec = nullptr;
-    // online autotuning: candidate plans tried on the first epochs with work
+    // online autotuning: candidate plans tried on the first epochs with work,
+    // scored by the epochs' wall time (host admission, replay and sync
+    // included: a fixed cost per epoch that small K pays more often) per
+    // cell update
     bool tuning = false;
     std::vector<Plan> cands;
-    std::vector<double> cand_ns;             // GPU ns per cell update, summed
+    std::vector<double> cand_ns;             // wall ns of the epochs, summed
     std::vector<uint64_t> cand_updates;
     int tune_epoch = 0, tune_per_plan = 3;
     // counters
@@ -783,7 +786,7 @@ static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
             uint64_t upd = 0;
             for (int i = 0; i < np; ++i) upd += (uint64_t)b->h_desc[i].n * b->h_desc[i].k;
             const size_t c = (size_t)(b->tune_epoch / b->tune_per_plan);
-            b->cand_ns[c] += 1e6 * ms;
+            b->cand_ns[c] += (double)(tdone - t);
             b->cand_updates[c] += upd;
             ++b->tune_epoch;
             const size_t nc = (size_t)(b->tune_epoch / b->tune_per_plan);

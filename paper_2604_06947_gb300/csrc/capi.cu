@@ -1693,6 +1693,7 @@ struct fqnm_fv {
     size_t n = 0, cap_n = 0;
     bool loaded = false;
     uint64_t launches = 0;
+    int k = 1;                              // time steps per launch
 };
 
 extern "C" fqnm_status fqnm_fv_create(const fqnm_flux* flux, double dx, double dt,
@@ -1787,11 +1788,38 @@ extern "C" fqnm_status fqnm_fv_load_device(fqnm_fv* f, const double* u, size_t n
     return fv_load(f, u, n, true);
 }
 
+extern "C" fqnm_status fqnm_fv_set_k(fqnm_fv* f, int k)
+{
+    if (!f) return set_error(FQNM_ERR_ARG, "null handle");
+    if (k < 1 || k > FV_TB_MAX_K) return set_error(FQNM_ERR_ARG, "K = %d outside 1..%d", k, FV_TB_MAX_K);
+    if (k > 1 && (f->nvars != 1 || f->boundary != FQNM_BC_PERIODIC))
+        return set_error(FQNM_ERR_ARG, "K > 1 needs a periodic scalar baseline");
+    f->k = k;
+    return FQNM_OK;
+}
+
 extern "C" fqnm_status fqnm_fv_step(fqnm_fv* f, uint64_t k)
 {
     if (!f) return set_error(FQNM_ERR_ARG, "null handle");
     if (!f->loaded) return set_error(FQNM_ERR_STATE, "fqnm_fv_step before load");
     const int periodic = f->boundary == FQNM_BC_PERIODIC;
+    if (f->k > 1) {
+        for (uint64_t done = 0; done < k;) {
+            const int kk = (int)std::min<uint64_t>((uint64_t)f->k, k - done);
+            void* in = f->u[f->cur];
+            void* out = f->u[1 - f->cur];
+            if (f->precision == 64)
+                CK(launch_fv_tb_f64(f->flux.kind, f->flux.a, f->flux.alpha, f->lambda,
+                                    (const double*)in, (double*)out, (int64_t)f->n, kk, f->stream));
+            else
+                CK(launch_fv_tb_f32(f->flux.kind, f->flux.a, f->flux.alpha, f->lambda,
+                                    (const float*)in, (float*)out, (int64_t)f->n, kk, f->stream));
+            f->cur = 1 - f->cur;
+            f->launches += 1;
+            done += (uint64_t)kk;
+        }
+        return FQNM_OK;
+    }
     for (uint64_t i = 0; i < k; ++i) {
         void* in = f->u[f->cur];
         void* out = f->u[1 - f->cur];

@@ -145,6 +145,12 @@ cudaError_t launch_fv_step_f64(int kind, double a, double alpha, double lambda,
 cudaError_t launch_fv_step_f32(int kind, double a, double alpha, double lambda,
                                const float* uin, float* uout, int64_t n,
                                int periodic, cudaStream_t st);
+// K steps per launch (periodic scalar problems; 1 <= K <= FV_TB_MAX_K)
+constexpr int FV_TB_MAX_K = 64;
+cudaError_t launch_fv_tb_f64(int kind, double a, double alpha, double lambda, const double* uin,
+                             double* uout, int64_t n, int K, cudaStream_t st);
+cudaError_t launch_fv_tb_f32(int kind, double a, double alpha, double lambda, const float* uin,
+                             float* uout, int64_t n, int K, cudaStream_t st);
 cudaError_t launch_euler_fv_f64(double gamma, double lambda, const double* uin,
                                 double* uout, int64_t n, cudaStream_t st);
 cudaError_t launch_euler_fv_f32(double gamma, double lambda, const float* uin,

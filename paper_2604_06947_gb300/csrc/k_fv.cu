@@ -2,11 +2,14 @@
 //
 // eq. classical_operator_definition:
 //     u_i <- u_i - lambda * (F_{i+1/2} - F_{i-1/2}),  F(uL,uR) = f+(uL) + f-(uR)
-// in float or double, one step per launch, each operation explicitly rounded
-// (no contraction) in the order
+// in float or double, each operation explicitly rounded (no contraction) in
+// the order
 //     Fr = f+(u_i) + f-(u_{i+1}),  Fl = f+(u_{i-1}) + f-(u_i),
 //     d = Fr - Fl,  u_i - lambda*d
 // with the split fluxes of eq. flux_splitting written as in the rule builder.
+// One step per launch, or (periodic scalar problems) K steps per launch in
+// tiles with a K-cell halo, the execution strategy of the integer kernel:
+// the same operations on the same values, so the two agree bit for bit.
 // The Euler variant uses the Roe flux of roe.cuh on [3][n], transmissive ends.
 #include "fqnm_internal.h"
 #include "roe.cuh"
@@ -21,29 +24,120 @@ struct FvParams {
     T a, alpha, lambda;
 };
 
-template <typename T>
-__device__ __forceinline__ T fsplit(const FvParams<T>& P, int sign, T u)
+template <typename T, int KIND>
+__device__ __forceinline__ T fsplit_k(const FvParams<T>& P, int sign, T u)
 {
     using A = Ar<T>;
-    switch (P.kind) {
-    case FQNM_FLUX_LINEAR_UPWIND: {
+    if (KIND == FQNM_FLUX_LINEAR_UPWIND) {
         const T c = sign > 0 ? (P.a > T(0) ? P.a : T(0)) : (P.a < T(0) ? P.a : T(0));
         return A::mul(c, u);
     }
-    case FQNM_FLUX_LINEAR_LF:
-    case FQNM_FLUX_BURGERS_LF: {
-        const T f = P.kind == FQNM_FLUX_LINEAR_LF ? A::mul(P.a, u)
-                                                  : A::mul(T(0.5), A::mul(u, u));
+    if (KIND == FQNM_FLUX_LINEAR_LF || KIND == FQNM_FLUX_BURGERS_LF) {
+        const T f = KIND == FQNM_FLUX_LINEAR_LF ? A::mul(P.a, u) : A::mul(T(0.5), A::mul(u, u));
         const T d = A::mul(P.alpha, u);
         return A::mul(T(0.5), sign > 0 ? A::add(f, d) : A::sub(f, d));
     }
-    case FQNM_FLUX_BURGERS_EO: {
+    if (KIND == FQNM_FLUX_BURGERS_EO) {
         const T w = sign > 0 ? (u > T(0) ? u : T(0)) : (u < T(0) ? u : T(0));
         return A::mul(T(0.5), A::mul(w, w));
     }
-    default:
-        return T(0);
+    return T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T fsplit(const FvParams<T>& P, int sign, T u)
+{
+    switch (P.kind) {
+    case FQNM_FLUX_LINEAR_UPWIND: return fsplit_k<T, FQNM_FLUX_LINEAR_UPWIND>(P, sign, u);
+    case FQNM_FLUX_LINEAR_LF: return fsplit_k<T, FQNM_FLUX_LINEAR_LF>(P, sign, u);
+    case FQNM_FLUX_BURGERS_LF: return fsplit_k<T, FQNM_FLUX_BURGERS_LF>(P, sign, u);
+    case FQNM_FLUX_BURGERS_EO: return fsplit_k<T, FQNM_FLUX_BURGERS_EO>(P, sign, u);
+    default: return T(0);
     }
+}
+
+// K steps per launch on a periodic line: a block of FV_TB_BLOCK threads
+// holds FV_TB_V consecutive cells per thread (a tile of FV_TB_TILE cells
+// starting K cells before the S = FV_TB_TILE - 2K cells it writes), takes
+// the neighbours' split fluxes by shuffle within a warp and through shared
+// memory between warps (one barrier per step); the tile's two end cells use
+// a ghost copy of themselves and lie outside the cells written.
+constexpr int FV_TB_V = 8, FV_TB_BLOCK = 128, FV_TB_TILE = FV_TB_V * FV_TB_BLOCK;
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(FV_TB_BLOCK)
+k_fv_tb(FvParams<T> P, const T* __restrict__ uin, T* __restrict__ uout, long long n, int K,
+        long long S)
+{
+    using A = Ar<T>;
+    constexpr int NW = FV_TB_BLOCK / 32;
+    __shared__ T shp[2][NW], shm[2][NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long start = (long long)blockIdx.x * S - K;
+    T u[FV_TB_V];
+#pragma unroll
+    for (int j = 0; j < FV_TB_V; ++j) {
+        long long g = (start + threadIdx.x * FV_TB_V + j) % n;
+        if (g < 0) g += n;
+        u[j] = uin[g];
+    }
+    for (int s = 0; s < K; ++s) {
+        T fp[FV_TB_V], fm[FV_TB_V];
+#pragma unroll
+        for (int j = 0; j < FV_TB_V; ++j) {
+            fp[j] = fsplit_k<T, KIND>(P, +1, u[j]);
+            fm[j] = fsplit_k<T, KIND>(P, -1, u[j]);
+        }
+        const int b = s & 1;
+        if (lane == 31) shp[b][w] = fp[FV_TB_V - 1];
+        if (lane == 0) shm[b][w] = fm[0];
+        __syncthreads();
+        T fpl = __shfl_up_sync(0xffffffffu, fp[FV_TB_V - 1], 1);
+        T fmr = __shfl_down_sync(0xffffffffu, fm[0], 1);
+        if (lane == 0) fpl = w > 0 ? shp[b][w - 1] : fp[0];
+        if (lane == 31) fmr = w < NW - 1 ? shm[b][w + 1] : fm[FV_TB_V - 1];
+        T Fl = A::add(fpl, fm[0]);
+#pragma unroll
+        for (int j = 0; j < FV_TB_V; ++j) {
+            const T Fr = A::add(fp[j], j < FV_TB_V - 1 ? fm[j + 1] : fmr);
+            u[j] = A::sub(u[j], A::mul(P.lambda, A::sub(Fr, Fl)));
+            Fl = Fr;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < FV_TB_V; ++j) {
+        const long long e = (long long)threadIdx.x * FV_TB_V + j;
+        const long long o = (long long)blockIdx.x * S + (e - K);
+        if (e >= K && e < K + S && o < n) uout[o] = u[j];
+    }
+}
+
+template <typename T>
+cudaError_t launch_fv_tb(const FvParams<T>& P, const T* uin, T* uout, long long n, int K,
+                         cudaStream_t st)
+{
+    if (K < 1 || K > FV_TB_MAX_K || n < 1) return cudaErrorInvalidValue;
+    const long long S = FV_TB_TILE - 2LL * K;
+    const long long blocks = (n + S - 1) / S;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    switch (P.kind) {
+    case FQNM_FLUX_LINEAR_UPWIND:
+        k_fv_tb<T, FQNM_FLUX_LINEAR_UPWIND><<<(unsigned)blocks, FV_TB_BLOCK, 0, st>>>(P, uin, uout, n, K, S);
+        break;
+    case FQNM_FLUX_LINEAR_LF:
+        k_fv_tb<T, FQNM_FLUX_LINEAR_LF><<<(unsigned)blocks, FV_TB_BLOCK, 0, st>>>(P, uin, uout, n, K, S);
+        break;
+    case FQNM_FLUX_BURGERS_LF:
+        k_fv_tb<T, FQNM_FLUX_BURGERS_LF><<<(unsigned)blocks, FV_TB_BLOCK, 0, st>>>(P, uin, uout, n, K, S);
+        break;
+    case FQNM_FLUX_BURGERS_EO:
+        k_fv_tb<T, FQNM_FLUX_BURGERS_EO><<<(unsigned)blocks, FV_TB_BLOCK, 0, st>>>(P, uin, uout, n, K, S);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    note_launches();
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -145,6 +239,19 @@ cudaError_t launch_fv_step_f32(int kind, double a, double alpha, double lambda,
     k_fv_step<float><<<grid_for(n, 256), 256, 0, st>>>(P, uin, uout, n, periodic);
     note_launches();
     return cudaGetLastError();
+}
+
+cudaError_t launch_fv_tb_f64(int kind, double a, double alpha, double lambda, const double* uin,
+                             double* uout, int64_t n, int K, cudaStream_t st)
+{
+    return launch_fv_tb<double>(FvParams<double>{kind, a, alpha, lambda}, uin, uout, n, K, st);
+}
+
+cudaError_t launch_fv_tb_f32(int kind, double a, double alpha, double lambda, const float* uin,
+                             float* uout, int64_t n, int K, cudaStream_t st)
+{
+    return launch_fv_tb<float>(FvParams<float>{kind, (float)a, (float)alpha, (float)lambda}, uin,
+                               uout, n, K, st);
 }
 
 cudaError_t launch_euler_fv_f64(double gamma, double lambda, const double* uin,

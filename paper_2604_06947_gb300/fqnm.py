@@ -127,6 +127,7 @@ PROTOTYPES = {
     "fqnm_fv_load": (_st, [_vp, _vp, C.c_size_t]),
     "fqnm_fv_load_device": (_st, [_vp, _vp, C.c_size_t]),
     "fqnm_fv_step": (_st, [_vp, C.c_uint64]),
+    "fqnm_fv_set_k": (_st, [_vp, C.c_int]),
     "fqnm_fv_observe": (_st, [_vp, _vp]),
     "fqnm_fv_observe_device": (_st, [_vp, _vp]),
     "fqnm_fv_launches": (_st, [_vp, C.POINTER(C.c_uint64)]),
@@ -513,6 +514,10 @@ def fqnm_fv_load_device(h: int, u_dev, n_cells: int):
 
 def fqnm_fv_step(h: int, k: int):
     _check(load().fqnm_fv_step(h, k))
+
+
+def fqnm_fv_set_k(h: int, k: int):
+    _check(load().fqnm_fv_set_k(h, k))
 
 
 def fqnm_fv_get_size(h: int):

@@ -276,6 +276,59 @@ def test_fv32_matches_cpu_and_fv64(orc, kind, a, alpha):
     F.fqnm_fv_destroy(h)
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("kind,a,alpha", [("burgers_lf", 0.0, 1.3), ("linear_upwind", 1.0, 0.0),
+                                          ("linear_lf", 0.5, 1.0), ("burgers_eo", 0.0, 1.3)])
+def test_fv_k_blocked_bitwise_equal_to_cpu(orc, prec, kind, a, alpha):
+    """K steps per launch (tiles with a K-cell halo) give the same bits as
+    the oracle's one-step loop: several K (ragged step counts, K above the
+    remaining steps), a ragged line and lines shorter than one tile."""
+    for n, K in ((7777, 2), (7777, 7), (7777, 64), (5, 3), (1000, 64)):
+        p = I.burgers_problem(n=n, steps=0)
+        u0 = p.delta * orc.quantise(p.u0, p.delta).astype(np.float64)
+        h = F.fqnm_fv_create(F.make_flux(kind, a=a, alpha=alpha), p.dx, p.dt, "periodic", prec)
+        F.fqnm_fv_set_k(h, K)
+        F.fqnm_fv_load(h, u0)
+        F.fqnm_fv_step(h, 150)
+        got = F.fqnm_fv_observe(h, p.n)
+        want = orc.fv_step(u0, kind, p.dx, p.dt, 150, a=a, alpha=alpha,
+                           precision="f%d" % prec)
+        assert np.array_equal(got, want.astype(np.float64)), (n, K)
+        F.fqnm_fv_destroy(h)
+
+
+def test_fv_k_blocked_full_size_and_errors():
+    """2^20 cells, 256 steps at K = 64 against the one-step kernel on the
+    device (bit for bit); K outside 1..64, K > 1 with transmissive ends or on
+    the Euler baseline are refused."""
+    p = I.burgers_problem()
+    u0 = p.delta * F.fqnm_quantise(p.u0, p.delta).astype(np.float64)
+    out = []
+    for K in (1, 64):
+        h = F.fqnm_fv_create(F.make_flux(p.flux, alpha=p.alpha), p.dx, p.dt, "periodic", 32)
+        F.fqnm_fv_set_k(h, K)
+        F.fqnm_fv_load(h, u0)
+        F.fqnm_fv_step(h, 256)
+        out.append(F.fqnm_fv_observe(h, p.n))
+        F.fqnm_fv_destroy(h)
+    assert np.array_equal(out[0], out[1])
+    h = F.fqnm_fv_create(F.make_flux(p.flux, alpha=p.alpha), p.dx, p.dt, "periodic", 32)
+    for bad in (0, 65):
+        with pytest.raises(F.FqnmError):
+            F.fqnm_fv_set_k(h, bad)
+    F.fqnm_fv_destroy(h)
+    h = F.fqnm_fv_create(F.make_flux(p.flux, alpha=p.alpha), p.dx, p.dt, "transmissive", 32)
+    with pytest.raises(F.FqnmError):
+        F.fqnm_fv_set_k(h, 2)
+    F.fqnm_fv_set_k(h, 1)
+    F.fqnm_fv_destroy(h)
+    q = I.sod_problem(n=256)
+    h = F.fqnm_fv_create(F.make_flux("euler_roe", gamma=q.gamma), q.dx, q.dt, "transmissive", 64)
+    with pytest.raises(F.FqnmError):
+        F.fqnm_fv_set_k(h, 4)
+    F.fqnm_fv_destroy(h)
+
+
 def test_euler_fv64_bitwise_equal_to_cpu(orc):
     p = I.sod_problem(n=2000)
     h = F.fqnm_fv_create(F.make_flux("euler_roe", gamma=G), p.dx, p.dt, "transmissive", 64)
