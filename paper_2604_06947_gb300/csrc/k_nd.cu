@@ -660,13 +660,10 @@ cudaError_t launch_walk3(const Ev& ev, const int32_t* qin, int32_t* qout, const 
     // One block fills an SM (registers), so blocks run in waves of one per
     // SM and a block of R slices takes R + 3K ticks: take the chunk count
     // whose waves x ticks is least.
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 152;
-    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     const long long xy = strips * rowblocks;
     long long R = nz, best = -1;
     for (long long c = 1; c <= nz && c <= 256; ++c) {
@@ -678,13 +675,10 @@ cudaError_t launch_walk3(const Ev& ev, const int32_t* qin, int32_t* qout, const 
     const long long blocks = strips * rowblocks * chunks;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     constexpr int smem = (int)sizeof(Walk3Smem<K, ROWS>);
-    static bool attr_set = false;                 // opt in above the 48 KB default once
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_walk3d<Ev, K, ROWS>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // opt in above the 48 KB default (a per-device attribute: set it for the
+    // current device at every launch)
+    e = cudaFuncSetAttribute(k_walk3d<Ev, K, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     k_walk3d<Ev, K, ROWS><<<(unsigned)blocks, 32 * ROWS, smem, st>>>(qin, qout, nx, ny, nz, strips,
                                                                      rowblocks, chunks, R, ev, err);
     note_launches();
