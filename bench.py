@@ -427,7 +427,9 @@ def other_workloads(F, torch, stream):
                      "effective_GBps": eff, "frac_of_hbm_peak": eff / peak,
                      "map": "closed form %d/%d" % (rule["num"], rule["den"])
                      if rule["evaluator"] == 2 else "table",
-                     "plan": {k: st[k] for k in ("layout", "cells_per_thread", "block", "k")}}
+                     "plan": dict({k: st[k] for k in ("layout", "cells_per_thread", "block", "k")},
+                                  kernel={1: "k_step_naive", 2: "k_step_tb",
+                                          4: "k_step_resident"}.get(st["kernel"], st["kernel"]))}
         s.close()
     # Sod: integer Roe and the FP64 Roe FV baseline
     p = I.sod_problem(n=1 << 16)

@@ -146,7 +146,12 @@ fqnm_status fqnm_set_stream(fqnm_solver* s, void* stream);
 /* Options (fqnm_option) that override the automatic execution plan.  Plans
  * differ in speed only: every plan gives bit-identical states. */
 typedef enum {
-    FQNM_OPT_KERNEL = 0,     /* 0 auto, 1 naive one-step, 2 temporal-blocked */
+    FQNM_OPT_KERNEL = 0,     /* 0 auto, 1 naive one-step, 2 temporal-blocked, 4 resident: a
+                                periodic line held whole by one block (V cells per thread,
+                                V in 1, 2, 4, 8 dividing n, n / V <= 1024 threads), every step
+                                of a call in one launch.  Auto takes 4 for periodic lines of
+                                at most 512 cells when no temporal-blocked plan option is set,
+                                else 2 (periodic) or 1. */
     FQNM_OPT_LAYOUT = 1,     /* 0 auto, 1 interleaved, 2 blocked (cells per thread contiguous) */
     FQNM_OPT_CELLS_PER_THREAD = 2, /* 4, 8, 16 or 32; 0 auto */
     FQNM_OPT_BLOCK = 3,      /* threads per block, multiple of 32, <= 512 (32: one warp, no barrier); 0 auto */
@@ -404,7 +409,7 @@ typedef struct {
     uint64_t launches;      /* kernels launched by step calls */
     uint64_t steps;
     uint64_t cell_updates;  /* n * steps */
-    int32_t kernel;         /* 1 naive, 2 temporal-blocked */
+    int32_t kernel;         /* 1 naive, 2 temporal-blocked, 3 Euler, 4 resident (k = 0) */
     int32_t layout, cells_per_thread, block, k;
     int32_t graph;          /* 1 if step loops are replayed from a CUDA graph */
 } fqnm_stats;

@@ -439,7 +439,8 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     if (!s) return set_error(FQNM_ERR_ARG, "null handle");
     switch (option) {
     case FQNM_OPT_KERNEL:
-        if (value < 0 || value > 2) return set_error(FQNM_ERR_ARG, "kernel must be 0..2");
+        if (value < 0 || value > 4 || value == 3)
+            return set_error(FQNM_ERR_ARG, "kernel must be 0, 1, 2 or 4");
         s->opt_kernel = (int)value; break;
     case FQNM_OPT_LAYOUT:
         if (value < 0 || value > 2) return set_error(FQNM_ERR_ARG, "layout must be 0..2");
@@ -657,6 +658,17 @@ static void replan(fqnm_solver* s)
     p.kernel = s->boundary == FQNM_BC_PERIODIC ? 2 : 1;
     if (s->opt_kernel == 1) p.kernel = 1;
     if (s->opt_kernel == 2 && s->boundary == FQNM_BC_PERIODIC) p.kernel = 2;
+    // a short periodic line fits one block: every step of a call in one
+    // launch.  Asked for, or by default up to RESIDENT_AUTO_CELLS when no
+    // temporal-blocked plan parameter was set: one block's step latency
+    // (about 140 ns at 256 cells, 210 ns at 1024) beats the tiled kernel's
+    // launches (about 5 us per 32 steps) only on the shortest lines.
+    const bool tb_opts = s->opt_layout || s->opt_v || s->opt_block || s->opt_k;
+    if (s->boundary == FQNM_BC_PERIODIC && s->grid.d == 1 && s->nvars == 1 &&
+        resident_v((int64_t)s->n) > 0 &&
+        (s->opt_kernel == 4 ||
+         (s->opt_kernel == 0 && !tb_opts && s->n <= (size_t)RESIDENT_AUTO_CELLS)))
+        p.kernel = 4;
     // default: the plan measured best on table and closed-form maps alike
     (void)table;
     p.layout = s->opt_layout ? s->opt_layout : LAYOUT_BLOCKED;
@@ -1069,6 +1081,19 @@ static fqnm_status step_scalar(fqnm_solver* s, uint64_t k)
             }
             s->cur = 1 - s->cur;
             s->launches += 1;
+        }
+        return FQNM_OK;
+    }
+    if (s->plan.kernel == 4) {
+        const uint64_t chunk = 1u << 16;               // steps per launch at most
+        for (uint64_t done = 0; done < k;) {
+            const uint64_t kk = std::min(chunk, k - done);
+            CK(launch_step_resident(s->rule, (const int32_t*)s->q[s->cur],
+                                    (int32_t*)s->q[1 - s->cur], (int64_t)s->n, (int64_t)kk,
+                                    s->d_err, s->stream));
+            s->cur = 1 - s->cur;
+            s->launches += 1;
+            done += kk;
         }
         return FQNM_OK;
     }
@@ -1618,6 +1643,12 @@ extern "C" fqnm_status fqnm_get_stats(fqnm_solver* s, fqnm_stats* out, int reset
     out->cells_per_thread = s->plan.v;
     out->block = s->plan.block;
     out->k = s->plan.k;
+    if (s->nvars == 1 && s->plan.kernel == 4) {          // one block holds the line
+        out->layout = LAYOUT_BLOCKED;
+        out->cells_per_thread = resident_v((int64_t)s->n);
+        out->block = out->cells_per_thread ? (int32_t)(s->n / out->cells_per_thread) : 0;
+        out->k = 0;
+    }
     out->graph = s->use_graph;
     if (reset) {
         s->launches = 0;

@@ -67,7 +67,7 @@ struct RuleView {
 
 // Execution plan of the scalar stepping kernels.
 struct Plan {
-    int kernel = 2;        // 1 naive, 2 temporal-blocked
+    int kernel = 2;        // 1 naive, 2 temporal-blocked, 4 resident (one block)
     int layout = LAYOUT_INTERLEAVED;
     int v = 8;             // cells per thread
     int block = 256;
@@ -115,6 +115,14 @@ cudaError_t launch_step_tb(const RuleView& r, const Plan& p, const int32_t* qin,
                            int32_t* qout, int64_t n, int k, unsigned* err,
                            cudaStream_t st);
 bool tb_plan_supported(const RuleView& r, const Plan& p);
+// A periodic line held whole by one block: cells per thread V (1, 2, 4, 8)
+// with V | n and n / V <= RESIDENT_MAX_THREADS, or 0 if none fits.
+constexpr int RESIDENT_MAX_THREADS = 1024;
+constexpr int RESIDENT_AUTO_CELLS = 512;   // the default plan's limit (measured crossover)
+int resident_v(int64_t n);
+// `steps` steps of the whole line in one launch.
+cudaError_t launch_step_resident(const RuleView& r, const int32_t* qin, int32_t* qout,
+                                 int64_t n, int64_t steps, unsigned* err, cudaStream_t st);
 
 // ---- k_reduce.cu ------------------------------------------------------------
 // acc[0..2] += (mass, tv, l1) of one variable (int32 or int64 states).

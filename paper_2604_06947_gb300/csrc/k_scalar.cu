@@ -25,6 +25,10 @@
 //      BLOCKED      lane l holds cells V*l + j: neighbours are mostly in the
 //                   same thread (two shuffles per V cells), best when the
 //                   map is a closed form and there is no gather.
+//  * k_step_resident: a short periodic line held whole by one block (n/V
+//    threads, V cells each), every step of the call in one launch: each
+//    step is exact over the whole line (no halo), so the latency per step
+//    is a few shuffles, one shared-memory exchange and one barrier.
 #include "tile_step.cuh"
 
 namespace fqnm {
@@ -114,6 +118,76 @@ cudaError_t launch_tb_t(const Ev& ev, int block, int pdl, const int* qin, int* q
     return cudaGetLastError();
 }
 
+// ---- resident kernel ----------------------------------------------------------
+
+// Thread t holds cells [tV, tV + V) of the n = blockDim.x * V cells.  The
+// last warp may be partial: its shuffles use the mask of its lanes.  Warp
+// edges and the periodic wrap go through shared memory: each warp publishes
+// p of its last cell and m of its first (double-buffered by step parity, one
+// barrier per step); warp 0's left neighbour is the last warp, and the last
+// warp's right neighbour is warp 0.
+template <class Ev, int V>
+__global__ void __launch_bounds__(RESIDENT_MAX_THREADS)
+k_step_resident(const int* __restrict__ qin, int* __restrict__ qout, long long steps, Ev ev,
+                unsigned* __restrict__ err)
+{
+    __shared__ int shp[2][RESIDENT_MAX_THREADS / 32], shm[2][RESIDENT_MAX_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    const int nl = w == nw - 1 ? (int)blockDim.x - 32 * (nw - 1) : 32;   // lanes of this warp
+    const unsigned mask = nl == 32 ? 0xffffffffu : ((1u << nl) - 1u);
+    const int wl = w == 0 ? nw - 1 : w - 1, wr = w == nw - 1 ? 0 : w + 1;
+    int q[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) q[j] = __ldg(qin + t * V + j);
+    unsigned acc = 0;
+    for (long long s = 0; s < steps; ++s) {
+        int p[V], m[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) ev(q[j], p[j], m[j], acc);
+        const int b = (int)(s & 1);
+        if (lane == nl - 1) shp[b][w] = p[V - 1];
+        if (Ev::HAS_M && lane == 0) shm[b][w] = m[0];
+        __syncthreads();
+        int pl = __shfl_up_sync(mask, p[V - 1], 1);
+        if (lane == 0) pl = shp[b][wl];
+        int mr = 0;
+        if (Ev::HAS_M) {
+            mr = __shfl_down_sync(mask, m[0], 1);
+            if (lane == nl - 1) mr = shm[b][wr];
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int l = j > 0 ? p[j - 1] : pl;
+            int d = l - p[j];
+            if (Ev::HAS_M) {
+                const int r = j < V - 1 ? m[j + 1] : mr;
+                d = Ev::FACE_MAX ? max(l, m[j]) - max(p[j], r) : d + m[j] - r;
+            }
+            q[j] += d;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) qout[t * V + j] = q[j];
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+}
+
+template <class Ev>
+cudaError_t launch_resident_t(const Ev& ev, int v, const int* qin, int* qout, long long n,
+                              long long steps, unsigned* err, cudaStream_t st)
+{
+    const unsigned threads = (unsigned)(n / v);
+    switch (v) {
+    case 1: k_step_resident<Ev, 1><<<1, threads, 0, st>>>(qin, qout, steps, ev, err); break;
+    case 2: k_step_resident<Ev, 2><<<1, threads, 0, st>>>(qin, qout, steps, ev, err); break;
+    case 4: k_step_resident<Ev, 4><<<1, threads, 0, st>>>(qin, qout, steps, ev, err); break;
+    case 8: k_step_resident<Ev, 8><<<1, threads, 0, st>>>(qin, qout, steps, ev, err); break;
+    default: return cudaErrorInvalidValue;
+    }
+    note_launches();
+    return cudaGetLastError();
+}
+
 template <class Ev>
 cudaError_t dispatch_tb(const Ev& ev, const Plan& p, const int* qin, int* qout,
                         long long n, int k, unsigned* err, cudaStream_t st)
@@ -141,6 +215,40 @@ bool tb_plan_supported(const RuleView& r, const Plan& p)
     if (p.block < 32 || p.block > TB_MAX_BLOCK || p.block % 32) return false;
     if (p.layout != LAYOUT_INTERLEAVED && p.layout != LAYOUT_BLOCKED) return false;
     return p.k >= 1 && 2LL * p.k < (long long)p.block * p.v;
+}
+
+int resident_v(int64_t n)
+{
+    // at most 256 threads where that fits (a step's latency, about 300 to
+    // 450 cycles, barely moves between 256 and 1024 threads), else the most
+    // cells per thread that fit one block
+    for (int v : {1, 2, 4, 8})
+        if (n % v == 0 && n / v <= 256) return v;
+    for (int v : {8, 4, 2, 1})
+        if (n % v == 0 && n / v <= RESIDENT_MAX_THREADS) return v;
+    return 0;
+}
+
+cudaError_t launch_step_resident(const RuleView& r, const int32_t* qin, int32_t* qout,
+                                 int64_t n, int64_t steps, unsigned* err, cudaStream_t st)
+{
+    const int v = resident_v(n);
+    if (v == 0 || n < 1 || steps < 1) return cudaErrorInvalidValue;
+    if (r.evaluator == EVAL_CLOSED_FORM && !r.has_m)
+        return launch_resident_t(EvClosedP{r.cf, r.lo, r.span}, v, qin, qout, n, steps, err, st);
+    if (!r.has_m)
+        return launch_resident_t(EvTableP{r.tabp, r.lo, r.span}, v, qin, qout, n, steps, err, st);
+    if (r.face_max) {
+        tb::EvTablePMMax ev;
+        ev.tab = r.tab2;
+        ev.lo = r.lo;
+        ev.span = r.span;
+        return launch_resident_t(ev, v, qin, qout, n, steps, err, st);
+    }
+    if (r.tab16)
+        return launch_resident_t(tb::EvTablePM16{r.tab16, r.lo, r.span}, v, qin, qout, n, steps,
+                                 err, st);
+    return launch_resident_t(EvTablePM{r.tab2, r.lo, r.span}, v, qin, qout, n, steps, err, st);
 }
 
 cudaError_t launch_step_naive(const RuleView& r, const int32_t* qin,

@@ -34,8 +34,11 @@ def run_and_compare(orc, p, q0, steps, every, boundary="periodic", **opts):
     while done < steps:
         k = min(every, steps - done)
         s.step(k)
-        q = orc.step(q, p.flux, p.delta, p.dx, p.dt, k, a=p.a, alpha=p.alpha,
-                     boundary=boundary)
+        if p.flux == "burgers_godunov":           # the oracle's two-point form
+            q = orc.step_two_point(q, p.flux, p.delta, p.dx, p.dt, k, boundary=boundary)
+        else:
+            q = orc.step(q, p.flux, p.delta, p.dx, p.dt, k, a=p.a, alpha=p.alpha,
+                         boundary=boundary)
         done += k
         got = s.state()
         assert np.array_equal(got.astype(np.int64), q), \
@@ -125,7 +128,7 @@ def test_linear_advection_1k_full(orc):
     assert q.sum() == gpu_q0(p).astype(np.int64).sum()
 
 
-PLANS = [dict(kernel=1)] + [
+PLANS = [dict(kernel=1), dict(kernel=4)] + [
     dict(kernel=2, layout=L, cells_per_thread=v, block=b, k=k)
     for L in (1, 2) for v in (4, 8, 16) for b in (64, 256) for k in (1, 7, 32)
 ] + [dict(kernel=2, layout=1, cells_per_thread=8, block=512, k=64),
@@ -144,6 +147,33 @@ def test_every_plan_bit_exact(orc, plan):
         run_and_compare(orc, p, q0, 75, 75, graph=0, **plan)
     p = I.high_frequency_problem(n=9001, steps=0)
     run_and_compare(orc, p, gpu_q0(p), 75, 75, graph=0, **plan)
+
+
+@pytest.mark.parametrize("flux", ["burgers_lf", "linear_upwind_closed", "linear_upwind_table",
+                                  "burgers_godunov", "burgers_lf_pack16"])
+def test_resident_kernel_bit_exact(orc, flux):
+    """The one-block kernel (every step of a call in one launch) with each
+    evaluator, on lines of one cell, a partial last warp, V = 1, 2, 4, 8 and
+    the full 1024 threads; one run (the default plan of a 96-cell line)
+    crosses the 65,536-step launch limit."""
+    opts = {"linear_upwind_closed": {}, "linear_upwind_table": {"closed_form": 0},
+            "burgers_lf_pack16": {"pack16": 1}}.get(flux, {})
+    for n in (1, 2, 33, 250, 1000, 1024, 4096, 6000, 8192):
+        if flux.startswith("linear"):
+            p = I.linear_advection_problem(n=n, steps=0)
+        else:
+            # delta 2^-12 keeps both maps within int16 for the packed table
+            p = I.burgers_problem(n=n, steps=0, delta=2.0 ** (-12 if "pack16" in flux else -16))
+            if flux == "burgers_godunov":
+                p.flux = "burgers_godunov"
+        q0 = gpu_q0(p)
+        _, st = run_and_compare(orc, p, q0, 150, 50, kernel=4, **opts)
+        assert st["kernel"] == 4 and st["k"] == 0, (n, st)
+        assert n % st["cells_per_thread"] == 0 and n // st["cells_per_thread"] == st["block"]
+    p = I.burgers_problem(n=96, steps=0)
+    if flux == "burgers_lf":                       # the default plan for a short line
+        _, st = run_and_compare(orc, p, gpu_q0(p), 70_000, 70_000)
+        assert st["kernel"] == 4
 
 
 def test_graph_replay_bit_exact(orc):
