@@ -130,6 +130,20 @@ struct NvtxRange {
         if (e_ != cudaSuccess) return cuda_error(e_, #call);       \
     } while (0)
 
+// A temporary device buffer, freed on every return path (CK returns early).
+template <typename T>
+struct DeviceScratch {
+    T* p = nullptr;
+    DeviceScratch() = default;
+    DeviceScratch(const DeviceScratch&) = delete;
+    DeviceScratch& operator=(const DeviceScratch&) = delete;
+    cudaError_t alloc(size_t count) { return cudaMalloc((void**)&p, count * sizeof(T)); }
+    ~DeviceScratch()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
 // ============================================================================
 // solver handle
 // ============================================================================
@@ -562,17 +576,15 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
         if (st != FQNM_OK) return st;
     }
     if (s->user_table || s->fplus) {
-        int32_t *dp = nullptr, *dm = nullptr;
-        CK(cudaMalloc(&dp, count * sizeof(int32_t)));
-        CK(cudaMalloc(&dm, count * sizeof(int32_t)));
-        CK(cudaMemcpyAsync(dp, s->user_p.data(), count * sizeof(int32_t),
+        DeviceScratch<int32_t> dp, dm;
+        CK(dp.alloc(count));
+        CK(dm.alloc(count));
+        CK(cudaMemcpyAsync(dp.p, s->user_p.data(), count * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s->stream));
-        CK(cudaMemcpyAsync(dm, s->user_m.data(), count * sizeof(int32_t),
+        CK(cudaMemcpyAsync(dm.p, s->user_m.data(), count * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s->stream));
-        CK(launch_copy_user_table(dp, dm, count, s->tab2, s->tabp, s->stream));
+        CK(launch_copy_user_table(dp.p, dm.p, count, s->tab2, s->tabp, s->stream));
         CK(cudaStreamSynchronize(s->stream));
-        cudaFree(dp);
-        cudaFree(dm);
     } else {
         // Godunov steps with the Engquist-Osher maps (and a max at each face)
         const int table_kind = s->flux.kind == FQNM_FLUX_BURGERS_GODUNOV ? FQNM_FLUX_BURGERS_EO
@@ -777,8 +789,9 @@ static fqnm_status autotune(fqnm_solver* s)
     }
     // stage 1: screen every candidate on a few launches from the loaded
     // state; stage 2: re-time the six fastest over about 1000 evolving steps
-    int32_t* sb = nullptr;
-    CK(cudaMalloc(&sb, s->n * sizeof(int32_t)));
+    DeviceScratch<int32_t> scratch;
+    CK(scratch.alloc(s->n));
+    int32_t* sb = scratch.p;
     int32_t* sa = (int32_t*)s->ckpt;              // restored by the caller
     std::vector<std::pair<float, Plan>> screened;
     const int layouts[2] = {LAYOUT_INTERLEAVED, LAYOUT_BLOCKED};
@@ -826,7 +839,6 @@ static fqnm_status autotune(fqnm_solver* s)
         const float t = median(ts[i]);
         if (t < best_t) { best_t = t; best = fin[i]; }
     }
-    cudaFree(sb);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned), s->stream));
     s->plan = best;
@@ -1792,17 +1804,16 @@ static fqnm_status fv_load(fqnm_fv* f, const double* u, size_t n, bool device)
     f->n = n;
     f->cur = 0;
     const double* src = u;
-    double* tmp = nullptr;
+    DeviceScratch<double> tmp;
     if (!device) {
-        CK(cudaMallocAsync((void**)&tmp, cnt * sizeof(double), f->stream));
-        CK(cudaMemcpyAsync(tmp, u, cnt * sizeof(double), cudaMemcpyHostToDevice, f->stream));
-        src = tmp;
+        CK(tmp.alloc(cnt));
+        CK(cudaMemcpyAsync(tmp.p, u, cnt * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+        src = tmp.p;
     }
     if (f->precision == 64)
         CK(cudaMemcpyAsync(f->u[0], src, cnt * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
     else
         CK(launch_convert_f64_to_f32(src, (float*)f->u[0], (int64_t)cnt, f->stream));
-    if (tmp) CK(cudaFreeAsync(tmp, f->stream));
     CK(cudaStreamSynchronize(f->stream));
     f->loaded = true;
     f->launches = 0;
