@@ -338,8 +338,8 @@ def fv_baselines(F, p, stream, torch):
     GPU, one step per launch, and FP32 with 64 steps per launch (the integer
     kernel's temporal blocking applied to the FP scheme: the ablation that
     separates the execution strategy from the arithmetic).  Each is
-    device-timed over the workload's steps, and its L1 distance to FQNM is
-    taken at every checkpoint (untimed)."""
+    device-timed over the workload's steps (median of 5), and its L1
+    distance to FQNM is taken at every checkpoint (untimed)."""
     steps, every = p.steps, 1000
     n = p.n
     q0 = F.fqnm_quantise(p.u0, p.delta)
@@ -360,13 +360,16 @@ def fv_baselines(F, p, stream, torch):
         F.fqnm_fv_load(h, u0)
         F.fqnm_fv_step(h, 64)
         stream.synchronize()
-        F.fqnm_fv_load(h, u0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        F.fqnm_fv_step(h, steps)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b)
+        runs = []
+        for _ in range(5):                       # load (host copy, synchronises) untimed
+            F.fqnm_fv_load(h, u0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            F.fqnm_fv_step(h, steps)
+            b.record(stream)
+            b.synchronize()
+            runs.append(a.elapsed_time(b))
+        ms = statistics.median(runs)
         F.fqnm_fv_load(h, u0)
         l1 = []
         for c in range(steps // every):
@@ -396,7 +399,7 @@ def _timed(stream, torch, fn, reps):
 
 def other_workloads(F, torch, stream):
     """The other workloads of the path, each timed on the device (median of
-    3), with inputs resident on the GPU:
+    5; the Sod runs, about 1.6 s each, once), with inputs resident on the GPU:
       - high-frequency transport, 2^24 cells, upwind nu = 0.9, 2000 steps
         (the verified closed form 9/10 replaces the table);
       - linear advection, 1024 cells, 2000 steps (a latency case);
@@ -418,7 +421,7 @@ def other_workloads(F, torch, stream):
             F.fqnm_step(s.h, p.steps)
         with torch.cuda.stream(stream):
             run()
-            t = _timed(stream, torch, run, 3)
+            t = _timed(stream, torch, run, 5)
         F.fqnm_sync(s.h)
         rule = F.fqnm_get_rule(s.h)
         eff = BYTES_PER_UPDATE * p.n * p.steps / t / 1e9
@@ -507,7 +510,7 @@ def nd_workload(F, torch, stream, dims, steps):
         with torch.cuda.stream(stream):
             s.load_field(u0, p.n, on_device=True)
             m0 = F.fqnm_invariants(s.h)["mass"][0]
-            t = _timed(stream, torch, lambda: F.fqnm_step(s.h, steps), 3)
+            t = _timed(stream, torch, lambda: F.fqnm_step(s.h, steps), 5)
         inv = F.fqnm_invariants(s.h)
         s.close()
         out[name] = {"seconds": t, "value": p.n * steps / t, "unit": UNIT,
@@ -541,7 +544,7 @@ def convergence_sweep(F, torch, stream, kmax: int = 14):
         du = torch.empty(n, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
             th = _timed(stream, torch, lambda: F.fqnm_hopf_lax(dx_, dy, dU, 0.3, nx=n, ny=y.size,
-                                                               u=du, stream=stream), 3)
+                                                               u=du, stream=stream), 5)
         ue = du.cpu().numpy()
         rows.append({"n_cells": n, "delta": p.delta, "time_steps": p.steps, "seconds": t,
                      "l1_vs_hopf_lax": float(p.dx * np.abs(u - ue).sum())})
