@@ -206,7 +206,9 @@ fqnm_status fqnm_quantise_device(const double* u, size_t n, double delta,
 /* Load the initial integer state (host or device pointer; int32 [n] for
  * scalar laws, int64 [3][n] for EULER_ROE).  Builds the transfer rule over
  * the loaded range (eq. flux_table, on the GPU), verifies any integer closed
- * form against it, and resets the step counter and boundary-flux totals. */
+ * form against it, and resets the step counter and boundary-flux totals.
+ * FQNM_ERR_ARG for n = 0; scalar states beyond +-2^30 (no headroom for a
+ * step's transfers in int32) are FQNM_ERR_OVERFLOW. */
 fqnm_status fqnm_load_states(fqnm_solver* s, const void* q, size_t n_cells);
 fqnm_status fqnm_load_states_device(fqnm_solver* s, const void* q,
                                     size_t n_cells);

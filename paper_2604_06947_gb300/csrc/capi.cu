@@ -892,6 +892,11 @@ static fqnm_status build_for_state(fqnm_solver* s, const void* q)
                              (long long)lo, (long long)hi, (long long)ulo, (long long)uhi);
         return build_rule(s, ulo, uhi);
     }
+    // the maps are built over [lo - margin, hi + margin] within +-2^30, which
+    // leaves a step's transfers room below the int32 limits
+    if (lo < INT32_MIN / 2 || hi > INT32_MAX / 2)
+        return set_error(FQNM_ERR_OVERFLOW, "states [%lld, %lld] beyond +-2^30 (int32 headroom)",
+                         (long long)lo, (long long)hi);
     const int64_t m = s->margin;
     return build_rule(s, std::max<int64_t>(lo - m, INT32_MIN / 2),
                       std::min<int64_t>(hi + m, INT32_MAX / 2));

@@ -78,6 +78,31 @@ def test_calls_out_of_order(fq):
     F.fqnm_destroy(h)
 
 
+def test_option_bounds(fq):
+    """Option values outside their sets are refused before any GPU work:
+    kernel 3 (the Euler kernel's number, not a plan), K of the FV baseline
+    outside 1..64, K > 1 on transmissive ends."""
+    h = F.fqnm_create(F.make_flux("linear_upwind", a=1.0), 2.0 ** -10, 0.01, 0.005)
+    for bad in (-1, 3, 5):
+        with pytest.raises(F.FqnmError) as e:
+            F.fqnm_set_option(h, "kernel", bad)
+        assert e.value.status == -1
+    for ok in (0, 1, 2, 4):
+        F.fqnm_set_option(h, "kernel", ok)
+    F.fqnm_destroy(h)
+    fv = F.fqnm_fv_create(F.make_flux("linear_upwind", a=1.0), 0.01, 0.005, "periodic", 32)
+    for bad in (0, 65):
+        with pytest.raises(F.FqnmError) as e:
+            F.fqnm_fv_set_k(fv, bad)
+        assert e.value.status == -1
+    F.fqnm_fv_set_k(fv, 64)
+    F.fqnm_fv_destroy(fv)
+    fv = F.fqnm_fv_create(F.make_flux("linear_upwind", a=1.0), 0.01, 0.005, "transmissive", 64)
+    with pytest.raises(F.FqnmError):
+        F.fqnm_fv_set_k(fv, 2)
+    F.fqnm_fv_destroy(fv)
+
+
 def _has_gpu():
     try:
         import torch

@@ -345,6 +345,30 @@ def test_range_escape_is_recovered_exactly(orc):
     s.close()
 
 
+@pytest.mark.parametrize("kernel", [1, 2, 4])
+def test_degenerate_inputs(orc, kernel):
+    """Empty input and states too close to the int32 limits are statuses; a
+    zero-step call changes nothing; a constant state is stationary on every
+    kernel (the flux differences vanish identically)."""
+    p = I.burgers_problem(n=256, steps=0)
+    s = F.Solver.for_problem(p, kernel=kernel)
+    with pytest.raises(F.FqnmError) as e:
+        F.fqnm_load_states(s.h, np.zeros(0, dtype=np.int32))
+    assert e.value.status == -1
+    with pytest.raises(F.FqnmError) as e:
+        s.load(np.full(256, 2 ** 31 - 100, dtype=np.int32))
+    assert e.value.status == -4
+    q0 = gpu_q0(p)
+    s.load(q0)
+    s.step(0)
+    assert np.array_equal(s.state(), q0)
+    s.load(np.full(256, 12345, dtype=np.int32))
+    s.step(333)
+    assert (s.state() == 12345).all()
+    assert s.stats()["kernel"] == kernel
+    s.close()
+
+
 def test_range_escape_without_recovery_is_a_status(orc):
     p = escaping_problem()
     s = F.Solver.for_problem(p, margin=0, recover=0)
