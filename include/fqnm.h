@@ -364,8 +364,10 @@ fqnm_status fqnm_set_grid(fqnm_solver* s, int d, const size_t* dims);
  * x[nx], y[ny], U0y[ny] in; u[nx] and idx[nx] (int64, may be NULL) out.
  * on_device = 1: all arrays are device pointers and the call is
  * asynchronous on `stream` (NULL: the legacy default stream); 0: host arrays,
- * copied, and the call synchronises.  FQNM_ERR_ARG for a null array, empty
- * input or t not positive and finite. */
+ * copied, and the call synchronises.  Partial minima over chunks of the
+ * candidates take stream-ordered device scratch (16 bytes per point and
+ * chunk, freed on the stream).  FQNM_ERR_ARG for a null array, empty input
+ * or t not positive and finite. */
 fqnm_status fqnm_hopf_lax(const double* x, size_t nx, const double* y,
                           const double* U0y, size_t ny, double t, double* u,
                           int64_t* idx, int on_device, void* stream);
