@@ -139,7 +139,11 @@ cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
         P.inv_delta[k] = 1.0 / delta[k];
     }
     P.rounding = rounding;
-    const int block = 128;
+    // one warp per block: the warps (segments of 30 cells) then spread over
+    // the SMs one at a time, so a grid smaller than the GPU loads every SM
+    // within one warp of the others (2^16 cells: 14 or 15 warps per SM,
+    // against 12 or 16 with 4-warp blocks)
+    const int block = 32;
     const long long warps = (n + EULER_OWN - 1) / EULER_OWN;
     const long long grid = (warps * 32 + block - 1) / block;
     k_euler_step<<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);

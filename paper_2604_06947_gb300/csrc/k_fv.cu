@@ -205,10 +205,11 @@ __global__ void k_euler_fv(T g, T lambda, const T* __restrict__ uin,
         uout[k * n + c] = A::sub(uin[k * n + c], A::mul(lambda, A::sub(Fr[k], Fl[k])));
 }
 
+// one warp per block (as the integer Euler kernel): a grid smaller than the
+// GPU then loads every SM within one warp of the others
 static unsigned euler_fv_grid(long long n)
 {
-    const long long warps = (n + EULER_FV_OWN - 1) / EULER_FV_OWN;
-    return (unsigned)((warps * 32 + 127) / 128);
+    return (unsigned)((n + EULER_FV_OWN - 1) / EULER_FV_OWN);
 }
 
 template <typename A, typename B>
@@ -257,7 +258,7 @@ cudaError_t launch_fv_tb_f32(int kind, double a, double alpha, double lambda, co
 cudaError_t launch_euler_fv_f64(double gamma, double lambda, const double* uin,
                                 double* uout, int64_t n, cudaStream_t st)
 {
-    k_euler_fv<double><<<euler_fv_grid(n), 128, 0, st>>>(gamma, lambda, uin, uout, n);
+    k_euler_fv<double><<<euler_fv_grid(n), 32, 0, st>>>(gamma, lambda, uin, uout, n);
     note_launches();
     return cudaGetLastError();
 }
@@ -265,7 +266,7 @@ cudaError_t launch_euler_fv_f64(double gamma, double lambda, const double* uin,
 cudaError_t launch_euler_fv_f32(double gamma, double lambda, const float* uin,
                                 float* uout, int64_t n, cudaStream_t st)
 {
-    k_euler_fv<float><<<euler_fv_grid(n), 128, 0, st>>>((float)gamma, (float)lambda,
+    k_euler_fv<float><<<euler_fv_grid(n), 32, 0, st>>>((float)gamma, (float)lambda,
                                                       uin, uout, n);
     note_launches();
     return cudaGetLastError();
