@@ -709,7 +709,7 @@ def run_reference(args):
                            % REF_SAMPLE_STEPS},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d cells x %d time steps per bench step"
-                                   % (p.n, REF_SAMPLE_STEPS)},
+                                   % (p.n, REF_SAMPLE_STEPS), "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
