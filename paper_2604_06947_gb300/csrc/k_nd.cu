@@ -674,28 +674,32 @@ cudaError_t launch_walk3(const Ev& ev, const int32_t* qin, int32_t* qout, const 
     const long long nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
     const long long strips = (nx + (WALK_COLS - 2 * K) - 1) / (WALK_COLS - 2 * K);
     const long long rowblocks = (ny + (ROWS - 2 * K) - 1) / (ROWS - 2 * K);
-    // One block fills an SM (registers), so blocks run in waves of one per
-    // SM and a block of R slices takes R + 3K ticks: take the chunk count
-    // whose waves x ticks is least.
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    // Blocks run in waves of `slots` (the SMs times the blocks each holds)
+    // and a block of R slices takes R + 3K ticks: take the chunk count whose
+    // waves x ticks is least.
+    constexpr int smem = (int)sizeof(Walk3Smem<K, ROWS>);
+    // opt in above the 48 KB default (a per-device attribute: set it for the
+    // current device at every launch)
+    cudaError_t e = cudaFuncSetAttribute(k_walk3d<Ev, K, ROWS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk3d<Ev, K, ROWS>,
+                                                          32 * ROWS, smem);
     if (e != cudaSuccess) return e;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
     const long long xy = strips * rowblocks;
     long long R = nz, best = -1;
     for (long long c = 1; c <= nz && c <= 256; ++c) {
         const long long r = (nz + c - 1) / c, chunks = (nz + r - 1) / r;
-        const long long cost = ((xy * chunks + sms - 1) / sms) * (r + 3 * K);
+        const long long cost = ((xy * chunks + slots - 1) / slots) * (r + 3 * K);
         if (best < 0 || cost < best) { best = cost; R = r; }
     }
     const long long chunks = (nz + R - 1) / R;
     const long long blocks = strips * rowblocks * chunks;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    constexpr int smem = (int)sizeof(Walk3Smem<K, ROWS>);
-    // opt in above the 48 KB default (a per-device attribute: set it for the
-    // current device at every launch)
-    e = cudaFuncSetAttribute(k_walk3d<Ev, K, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
     k_walk3d<Ev, K, ROWS><<<(unsigned)blocks, 32 * ROWS, smem, st>>>(qin, qout, nx, ny, nz, strips,
                                                                      rowblocks, chunks, R, ev, err);
     note_launches();
