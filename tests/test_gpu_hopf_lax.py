@@ -53,6 +53,20 @@ def test_ties_go_to_the_smallest_index_and_nan_candidates():
         assert idx[0] == want, U
 
 
+def test_ties_across_candidate_chunks():
+    """The candidates listed twice (40,000 entries, split into many chunks):
+    every minimum occurs in two chunks, and the first copy's index wins, as
+    in the oracle's single scan."""
+    y1, U1 = I.sine_candidates(20000 // 3)
+    y = np.concatenate([y1, y1])
+    U = np.concatenate([U1, U1])
+    x = np.linspace(0.0, 1.0, 67)
+    u, idx = F.fqnm_hopf_lax(x, y, U, 0.3)
+    wu, widx = HL.hopf_lax(x, y, U, 0.3)
+    assert np.array_equal(idx, widx) and np.array_equal(u, wu)
+    assert (idx < y1.size).all()
+
+
 def test_device_variant_dense_grid_sampled():
     """Device arrays on a torch stream at 2^14 points x 3 * 2^16 candidates;
     512 sampled rows against the oracle."""
