@@ -491,9 +491,9 @@ k_walk2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long
     if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
 }
 
-// Rows per warp R: enough warps for about 24 per SM (latency hiding),
-// between 4K (the walk re-reads 2K halo rows and fills its pipeline for K
-// more ticks per R rows) and 256.
+// Rows per warp R (at least 4K: a walk re-reads 2K halo rows and fills its
+// pipeline for K more ticks per R rows) chosen against the waves the grid
+// needs; see the cost rule below.
 template <class Ev, int K>
 cudaError_t launch_walk(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
                         unsigned* err, cudaStream_t st)
