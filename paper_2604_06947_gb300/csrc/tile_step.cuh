@@ -142,10 +142,27 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
     // completed and its stores are visible (a no-op otherwise).
     asm volatile("griddepcontrol.wait;" ::: "memory");
     int q[V];
+    // blocked layout: a thread's V cells are consecutive, so an aligned run
+    // inside [0, n) loads as int4 vectors (16-byte loads, fully used);
+    // wrapped or misaligned runs load cell by cell
+    const long long c0 = start + (long long)threadIdx.x * V;
+    const bool vec = LAYOUT == LAYOUT_BLOCKED && V % 4 == 0 && c0 >= 0 && c0 + V <= n &&
+                     (reinterpret_cast<uintptr_t>(qin + c0) & 15) == 0;
+    if (vec) {
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-        const long long gi = wrap_index(start + cell_of<LAYOUT, V>(j), n);
-        q[j] = FQNM_IN_RANGE(gi, n, err) ? __ldg(qin + gi) : 0;
+        for (int j = 0; j < V; j += 4) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(qin + c0 + j));
+            q[j] = v.x;
+            q[j + 1] = v.y;
+            q[j + 2] = v.z;
+            q[j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const long long gi = wrap_index(start + cell_of<LAYOUT, V>(j), n);
+            q[j] = FQNM_IN_RANGE(gi, n, err) ? __ldg(qin + gi) : 0;
+        }
     }
 
     unsigned acc = 0;
@@ -217,13 +234,35 @@ __device__ __forceinline__ void tile_step(const int* __restrict__ qin,
     // let the next step launch start its blocks (they wait for this grid)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-    // cells [K, K+S) of the block are exact after K steps
+    // cells [K, K+S) of the block are exact after K steps; in the blocked
+    // layout a thread's aligned groups of 4 inside that range and inside
+    // [0, n) store as int4 vectors
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-        const long long e = cell_of<LAYOUT, V>(j);
-        if (e >= K && e < K + S) {
+    for (int j0 = 0; j0 < V; j0 += (LAYOUT == LAYOUT_BLOCKED && V % 4 == 0) ? 4 : 1) {
+        if (LAYOUT == LAYOUT_BLOCKED && V % 4 == 0) {
+            const long long e = (long long)threadIdx.x * V + j0;
             const long long o = tile * S + (e - K);
-            if (o < n && FQNM_IN_RANGE(o, n, err)) qout[o] = q[j];
+            if (e >= K && e + 4 <= K + S && o + 4 <= n &&
+                (reinterpret_cast<uintptr_t>(qout + o) & 15) == 0) {
+                if (FQNM_IN_RANGE(o + 3, n, err))
+                    *reinterpret_cast<int4*>(qout + o) =
+                        make_int4(q[j0], q[j0 + 1], q[j0 + 2], q[j0 + 3]);
+                continue;
+            }
+#pragma unroll
+            for (int j = j0; j < j0 + 4; ++j) {
+                const long long ej = (long long)threadIdx.x * V + j;
+                if (ej >= K && ej < K + S) {
+                    const long long oj = tile * S + (ej - K);
+                    if (oj < n && FQNM_IN_RANGE(oj, n, err)) qout[oj] = q[j];
+                }
+            }
+        } else {
+            const long long e = cell_of<LAYOUT, V>(j0);
+            if (e >= K && e < K + S) {
+                const long long o = tile * S + (e - K);
+                if (o < n && FQNM_IN_RANGE(o, n, err)) qout[o] = q[j0];
+            }
         }
     }
     if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
