@@ -75,11 +75,25 @@ k_fv_tb(FvParams<T> P, const T* __restrict__ uin, T* __restrict__ uout, long lon
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long start = (long long)blockIdx.x * S - K;
     T u[FV_TB_V];
+    // a thread's cells are consecutive: an aligned run inside [0, n) loads as
+    // 16-byte vectors (as in the integer kernel), a wrapped one cell by cell
+    constexpr int PER16 = 16 / (int)sizeof(T);
+    const long long c0 = start + (long long)threadIdx.x * FV_TB_V;
+    if (c0 >= 0 && c0 + FV_TB_V <= n && (reinterpret_cast<uintptr_t>(uin + c0) & 15) == 0) {
 #pragma unroll
-    for (int j = 0; j < FV_TB_V; ++j) {
-        long long g = (start + threadIdx.x * FV_TB_V + j) % n;
-        if (g < 0) g += n;
-        u[j] = uin[g];
+        for (int j = 0; j < FV_TB_V; j += PER16) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(uin + c0 + j));
+            const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+            for (int k = 0; k < PER16; ++k) u[j + k] = e[k];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < FV_TB_V; ++j) {
+            long long g = (start + threadIdx.x * FV_TB_V + j) % n;
+            if (g < 0) g += n;
+            u[j] = uin[g];
+        }
     }
     for (int s = 0; s < K; ++s) {
         T fp[FV_TB_V], fm[FV_TB_V];
@@ -105,10 +119,24 @@ k_fv_tb(FvParams<T> P, const T* __restrict__ uin, T* __restrict__ uout, long lon
         }
     }
 #pragma unroll
-    for (int j = 0; j < FV_TB_V; ++j) {
-        const long long e = (long long)threadIdx.x * FV_TB_V + j;
+    for (int j0 = 0; j0 < FV_TB_V; j0 += PER16) {
+        const long long e = (long long)threadIdx.x * FV_TB_V + j0;
         const long long o = (long long)blockIdx.x * S + (e - K);
-        if (e >= K && e < K + S && o < n) uout[o] = u[j];
+        if (e >= K && e + PER16 <= K + S && o + PER16 <= n &&
+            (reinterpret_cast<uintptr_t>(uout + o) & 15) == 0) {
+            uint4 v;
+            T* w = reinterpret_cast<T*>(&v);
+#pragma unroll
+            for (int k = 0; k < PER16; ++k) w[k] = u[j0 + k];
+            *reinterpret_cast<uint4*>(uout + o) = v;
+            continue;
+        }
+#pragma unroll
+        for (int j = j0; j < j0 + PER16; ++j) {
+            const long long ej = (long long)threadIdx.x * FV_TB_V + j;
+            const long long oj = (long long)blockIdx.x * S + (ej - K);
+            if (ej >= K && ej < K + S && oj < n) uout[oj] = u[j];
+        }
     }
 }
 
