@@ -499,10 +499,9 @@ def nd_workload(F, torch, stream, dims, steps):
     p = I.burgers_nd_problem(dims, steps=steps)
     u0 = torch.from_numpy(p.u0).cuda()
     out = {"dims": list(dims), "n_cells": p.n, "time_steps": steps}
-    plans = [("default", {})] + ([("tile_64x32", {"nd_tile": 3}), ("one_step", {"kernel": 1})]
-                                 if len(dims) == 2 else
-                                 [("walk_k1", {"k": 1}), ("walk_k3", {"k": 3}),
-                                  ("one_step", {"kernel": 1})])
+    plans = [("default", {}), ("autotuned", {"autotune": 1})] + (
+        [("tile_64x32", {"nd_tile": 3}), ("one_step", {"kernel": 1})] if len(dims) == 2 else
+        [("walk_k1", {"k": 1}), ("walk_k3", {"k": 3}), ("one_step", {"kernel": 1})])
     for name, opt in plans:
         s = F.Solver.for_problem(p, **opt)
         s.set_grid(p.dims)
@@ -512,10 +511,13 @@ def nd_workload(F, torch, stream, dims, steps):
             m0 = F.fqnm_invariants(s.h)["mass"][0]
             t = _timed(stream, torch, lambda: F.fqnm_step(s.h, steps), 5)
         inv = F.fqnm_invariants(s.h)
+        st = F.fqnm_get_stats(s.h)
         s.close()
         out[name] = {"seconds": t, "value": p.n * steps / t, "unit": UNIT,
                      "effective_GBps": BYTES_PER_UPDATE * p.n * steps / t / 1e9,
-                     "mass_exact": inv["mass"][0] == m0}
+                     "mass_exact": inv["mass"][0] == m0,
+                     "plan": {"kernel": {1: "one step", 5: "walk", 6: "register tile"}.get(
+                         st["kernel"], st["kernel"]), "nd_tile": st["layout"], "k": st["k"]}}
     return out
 
 

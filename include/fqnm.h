@@ -159,7 +159,10 @@ typedef enum {
     FQNM_OPT_MARGIN = 5,     /* quanta added on each side of the loaded range (default 1024) */
     FQNM_OPT_CLOSED_FORM = 6,/* 1 (default): use a verified integer closed form when one exists */
     FQNM_OPT_RECOVER = 7,    /* 1 (default): on range escape widen the map and replay */
-    FQNM_OPT_AUTOTUNE = 8,   /* 1: time candidate plans at load and keep the fastest */
+    FQNM_OPT_AUTOTUNE = 8,   /* 1: time candidate plans at load and keep the fastest: 1-D
+                                temporal-blocked plans (cached per size class), or on a
+                                grid the walk depths and (2-D) register tiles, unless a d-D
+                                plan option (FQNM_OPT_ND_TILE, FQNM_OPT_K) was set */
     FQNM_OPT_GRAPH = 9,      /* 1 (default): replay long step loops from a CUDA graph */
     FQNM_OPT_PDL = 10,       /* 1 (default): chain step launches with programmatic dependent
                                 launch (the next launch's blocks start while the previous
@@ -413,7 +416,9 @@ typedef struct {
     uint64_t launches;      /* kernels launched by step calls */
     uint64_t steps;
     uint64_t cell_updates;  /* n * steps */
-    int32_t kernel;         /* 1 naive, 2 temporal-blocked, 3 Euler, 4 resident (k = 0) */
+    int32_t kernel;         /* 1 naive (or d-D one step), 2 temporal-blocked, 3 Euler,
+                               4 resident (k = 0), 5 d-D walk, 6 d-D register tile (layout =
+                               the FQNM_OPT_ND_TILE code, k = steps per launch) */
     int32_t layout, cells_per_thread, block, k;
     int32_t graph;          /* 1 if step loops are replayed from a CUDA graph */
 } fqnm_stats;

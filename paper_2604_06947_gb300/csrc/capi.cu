@@ -168,6 +168,7 @@ struct fqnm_solver {
     int qmask = 7;                          // Euler: components evolved as integers
     NdGrid grid{1, {0, 1, 1}};              // d > 1: the Cartesian step of Theorem (extension)
     int opt_nd_tile = 0;                    // 2-D tile shape (0: default)
+    int nd_tuned_tile = -1, nd_tuned_k = 0; // d-D plan kept by the autotuner (-1: none)
     int verify = 0;                         // check the conserved totals at each sync
     long long mass0[3] = {0, 0, 0};         // totals the check expects (plus boundary transfer)
 
@@ -774,9 +775,79 @@ static void write_tune_file()
     std::rename(tmp.c_str(), path);
 }
 
+// d-D plans: every walk depth the kernels support and (2-D) every register
+// tile at K = 2, 3, 4, each timed twice (interleaved) over about 32 steps
+// that evolve scratch copies of the loaded state.  The default plan (the
+// walk at K = 4 in 2-D, 2 in 3-D) stays unless another is more than 3 %
+// faster per step: short timings on a large grid drift by about that much.
+static fqnm_status autotune_nd(fqnm_solver* s)
+{
+    if (s->opt_kernel == 1 || s->opt_nd_tile != 0 || s->opt_k != 0) return FQNM_OK;
+    struct Cand { int tile, k; };
+    std::vector<Cand> cands;
+    if (s->grid.d == 2) {
+        for (int k : {2, 3, 4, 6, 8}) cands.push_back({ND_WALK, k});
+        for (int t = 1; t <= 5; ++t)
+            for (int k : {2, 3, 4}) cands.push_back({t, k});
+    } else {
+        for (int k = 1; k <= 4; ++k) cands.push_back({ND_WALK, k});
+    }
+    DeviceScratch<int32_t> scratch;
+    CK(scratch.alloc(s->n));
+    int32_t* sa = (int32_t*)s->ckpt;              // restored by the caller
+    int32_t* sb = scratch.p;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    auto launch = [&](const Cand& c, const int32_t* in, int32_t* out) {
+        if (c.tile == ND_WALK)
+            return s->grid.d == 3 ? launch_walk3d(s->rule, in, out, s->grid, c.k, s->d_err, s->stream)
+                                  : launch_walk2d(s->rule, in, out, s->grid, c.k, s->d_err, s->stream);
+        NdPlan p;
+        p.blocked = 1;
+        p.walk = 0;
+        p.shape = c.tile;
+        p.k = c.k;
+        return launch_step2d_tb(s->rule, p, in, out, s->grid, c.k, s->d_err, s->stream);
+    };
+    std::vector<float> best(cands.size(), 1e30f);
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)
+        for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+            const Cand& c = cands[i];
+            const int launches = std::max(2, 32 / c.k);
+            e = cudaMemcpyAsync(sa, s->q[s->cur], s->n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                s->stream);
+            if (e == cudaSuccess) e = launch(c, sa, sb);                    // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(a, s->stream);
+            for (int j = 0; j < launches && e == cudaSuccess; ++j)
+                e = launch(c, (j & 1) ? sb : sa, (j & 1) ? sa : sb);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess) best[i] = std::min(best[i], ms / (launches * (float)c.k));
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_error(e, "autotune_nd");
+    const int dflt_k = s->grid.d == 3 ? 2 : 4;
+    size_t dflt = 0, pick = 0;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if (cands[i].tile == ND_WALK && cands[i].k == dflt_k) dflt = i;
+        if (best[i] < best[pick]) pick = i;
+    }
+    if (best[pick] * 1.03f > best[dflt]) pick = dflt;
+    s->nd_tuned_tile = cands[pick].tile;
+    s->nd_tuned_k = cands[pick].k;
+    CK(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned), s->stream));
+    return FQNM_OK;
+}
+
 static fqnm_status autotune(fqnm_solver* s)
 {
-    if (s->plan.kernel != 2 || s->grid.d > 1) return FQNM_OK;
+    if (s->grid.d > 1) return autotune_nd(s);
+    if (s->plan.kernel != 2) return FQNM_OK;
     TuneKey key{(int64_t)bit_length((uint64_t)s->n), s->rule.evaluator, s->rule.has_m};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -1052,6 +1123,13 @@ static NdPlan nd_plan(const fqnm_solver* s)
 {
     NdPlan p;
     p.blocked = s->opt_kernel != 1;
+    // the autotuner's plan, unless a plan option was set explicitly
+    if (p.blocked && s->nd_tuned_tile >= 0 && s->opt_nd_tile == 0 && s->opt_k == 0) {
+        p.walk = s->nd_tuned_tile == ND_WALK;
+        if (!p.walk) p.shape = s->nd_tuned_tile;
+        p.k = s->nd_tuned_k;
+        return p;
+    }
     p.walk = s->grid.d == 3 || s->opt_nd_tile == 0 || s->opt_nd_tile == ND_WALK;
     if (!p.walk) p.shape = s->opt_nd_tile;
     const int lim = s->grid.d == 3 ? 4
@@ -1660,6 +1738,14 @@ extern "C" fqnm_status fqnm_get_stats(fqnm_solver* s, fqnm_stats* out, int reset
     out->cells_per_thread = s->plan.v;
     out->block = s->plan.block;
     out->k = s->plan.k;
+    if (s->nvars == 1 && s->grid.d > 1) {                // the d-D plan
+        const NdPlan np = nd_plan(s);
+        out->kernel = !np.blocked ? 1 : (np.walk ? 5 : 6);
+        out->layout = np.walk ? ND_WALK : np.shape;
+        out->cells_per_thread = 0;
+        out->block = 0;
+        out->k = np.blocked ? np.k : 1;
+    }
     if (s->nvars == 1 && s->plan.kernel == 4) {          // one block holds the line
         out->layout = LAYOUT_BLOCKED;
         out->cells_per_thread = resident_v((int64_t)s->n);

@@ -124,6 +124,26 @@ def test_full_size_3d_grid(orc):
     s.close()
 
 
+@pytest.mark.parametrize("dims", [(150, 70), (96, 64, 40)])
+def test_autotuned_nd_plan_bit_exact(orc, dims):
+    """The d-D autotuner's choice (walk depths and, in 2-D, register tiles,
+    timed at load) gives the oracle's states; an explicit K turns it off."""
+    p = I.burgers_nd_problem(dims)
+    shape = dims[::-1]
+    q0 = orc.quantise(p.u0, p.delta).reshape(shape)
+    s = solver_for(p, autotune=1).load(q0.reshape(-1))
+    st = s.stats()
+    assert st["kernel"] in ((5,) if len(dims) == 3 else (5, 6)) and st["k"] >= 1
+    s.step(13)
+    want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 13, alpha=p.alpha)
+    assert np.array_equal(s.state().reshape(shape), want)
+    s.close()
+    s = solver_for(p, autotune=1, k=3).load(q0.reshape(-1))
+    st = s.stats()
+    assert st["kernel"] == 5 and st["k"] == 3
+    s.close()
+
+
 def test_linear_upwind_closed_form_2d(orc):
     """Upwind a = 1 at nu = 0.45 per axis (d nu = 0.9): phi+ = R(9 q / 20),
     the verified closed form replaces the table."""
