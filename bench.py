@@ -80,15 +80,18 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_counters(kernel_tag: str, src_digest: str) -> dict:
+def profiled_counters(kernel_tag: str, src_digest: str, workload: str = "") -> dict:
     """Per-launch counters from the committed ncu summary (profiles/traffic.txt),
-    if they were taken on the current kernel sources (else {})."""
+    if they were taken on the current kernel sources (else {}); with
+    `workload`, only a line captured on that workload."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         for line in open(path):
             if line.lstrip().startswith("#"):
                 continue
             f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+            if workload and f.get("workload") != workload:
+                continue
             if f.get("kernel") == kernel_tag and f.get("src_sha") == src_digest:
                 return {k: float(v) for k, v in f.items()
                         if k in ("dram_bytes_per_launch", "warp_instructions_per_launch")}
@@ -234,6 +237,7 @@ def run_gpu(args):
     launches = F.fqnm_kernel_launches() - launches0
     stats = F.fqnm_get_stats(s.h)
     clk = clocks.stop()
+    final_q = s.state()              # the last timed step's result (parity, untimed)
 
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     value = whole_job_rate(n * T * args.steps, world, total_ms / 1e3)
@@ -241,12 +245,11 @@ def run_gpu(args):
     # dominant kernel: the temporal-blocked step, launched only inside the
     # stepping region; average launch duration from the events around it
     avg_launch_s = (sum(region_ms) / 1e3) / max(step_launches, 1)
-    bytes_per_launch = BYTES_PER_UPDATE * n * (T * args.steps) / max(step_launches, 1)
-    achieved = bytes_per_launch / avg_launch_s / 1e9
-    peak, peak_kind = measured_peak()
+    updates_per_launch = n * (T * args.steps) / max(step_launches, 1)
     kernel_tag = "k_step_tb:L%d:V%d" % (stats["layout"], stats["cells_per_thread"])
-    counters = profiled_counters(kernel_tag, B.kernel_digest())
-    traffic = counters.get("dram_bytes_per_launch")
+    counters = profiled_counters(kernel_tag, B.kernel_digest(),
+                                 "burgers_lf_2^20_cells_K%d" % stats["k"])
+    roofline = stepping_roofline(counters, updates_per_launch, avg_launch_s, clk, kernel_tag)
 
     # end to end through the C ABI with host buffers (rank-local)
     u0_host = torch.from_numpy(p.u0).pin_memory()
@@ -269,8 +272,25 @@ def run_gpu(args):
     if rank == 0:
         baselines = fv_baselines(F, p, stream, torch) if not args.no_fv else None
         serving = serving_block(torch) if not args.no_serving else None
-        workloads = other_workloads(F, torch, stream) if not args.no_workloads else None
+        if serving is not None and world == 1 and not args.no_cpu:
+            dev_s = serving.pop("_dev")
+            serving["cpu_baseline"], serving["_oracle_check"] = serving_cpu_baseline(
+                lambda i: dev_s.result(i).cpu().numpy(), serving.pop("_reqs"))
+        elif serving is not None:
+            serving.pop("_dev")
+            serving.pop("_reqs")
+        finals = {}
+        workloads = (other_workloads(F, torch, stream, clk, finals)
+                     if not args.no_workloads else None)
         cpu = cpu_baseline(p) if (world == 1 and not args.no_cpu) else None
+        if cpu:
+            # the CPU-baseline leg also checks the GPU's results against the
+            # oracle, untimed: the timed workload's final state, the
+            # high-frequency line's, and the serving stream's sampled requests
+            parity = oracle_parity(p, final_q, cpu.pop("_q_sample"), finals)
+            sod_accuracy(finals, workloads)
+            if serving is not None:
+                parity["serving_stream"] = serving.pop("_oracle_check", None)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -285,14 +305,7 @@ def run_gpu(args):
                                 "cells_per_thread": stats["cells_per_thread"],
                                 "block": stats["block"], "k": stats["k"],
                                 "graph": stats["graph"]}},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind,
-                         "kernel": kernel_tag,
-                         "bytes_model": "8 B per cell update (int32 read + write), "
-                                        "x cells x steps per launch; effective under "
-                                        "temporal blocking",
-                         "issue": issue_roofline(counters, avg_launch_s, clk)},
+            "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "gpu_launches": launches,
@@ -300,11 +313,22 @@ def run_gpu(args):
         }
         if cpu:
             result["cpu_baseline"] = cpu
+            result["parity"] = parity
+            # a compact copy inside cpu_baseline, the leg that produced it
+            cpu["parity"] = {"all_equal": parity["all_equal"],
+                             "checks": {k: (v.get("equal") if k != "serving_stream" else
+                                            "%d/%d" % (v["requests_equal"],
+                                                       v["requests_checked"]))
+                                        for k, v in parity.items()
+                                        if isinstance(v, dict) and v is not None}}
+        if workloads and "roofline" in workloads.get("high_frequency_16m", {}):
+            result["roofline"]["high_frequency_16m"] = {
+                k: workloads["high_frequency_16m"]["roofline"].get(k)
+                for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                          "effective_hbm", "dram")}
         if baselines:
             result["fv_baseline"] = baselines
         if serving:
-            if world == 1 and not args.no_cpu:
-                serving["cpu_baseline"] = serving_cpu_baseline()
             result["serving"] = serving
         if workloads:
             result["workloads"] = workloads
@@ -317,20 +341,56 @@ def run_gpu(args):
     return result
 
 
-def issue_roofline(counters: dict, launch_s: float, clk: dict):
-    """The bound the stepping kernel actually meets: warp instructions per
-    launch (committed ncu count on the same sources) over the live launch
-    time, against 4 warp instructions per SM per cycle at the sampled clock."""
-    wi = counters.get("warp_instructions_per_launch")
-    if not wi or not clk or not clk.get("sm_mhz"):
-        return None
+def issue_peak(clk: dict):
+    """Warp instructions per second the GPU can issue: 4 per SM per cycle
+    (one scheduler per SM sub-partition) at the sampled SM clock."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    peak = 4.0 * sms * clk["sm_mhz"] * 1e6
-    achieved = wi / launch_s
-    return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s",
-            "frac": achieved / peak, "warp_instructions_per_launch": wi,
-            "peak_model": "4 issue slots per SM per cycle x SMs x sampled SM clock"}
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    return 4.0 * sms * mhz * 1e6
+
+
+def stepping_roofline(counters: dict, updates_per_launch: float, launch_s: float,
+                      clk: dict, kernel_tag: str) -> dict:
+    """The roofline of a temporal-blocked stepping kernel, against the bound
+    it actually meets.
+
+    The kernel keeps a tile in registers for K steps, so it reads and writes
+    the state in HBM once per K steps: HBM is not its bound (DRAM traffic,
+    from the committed ncu counters, is about 1/K of the effective bytes).
+    It is bound by instruction issue on on-chip data: `achieved` is the warp
+    instructions one launch executes (committed ncu count on the same
+    kernel sources) over the live launch time, `peak` 4 warp instructions
+    per SM per cycle at the sampled clock.  The effective-byte figure
+    (8 B per cell update over the launch time, against the measured HBM copy
+    peak) and the physical DRAM rate are reported beside it, named as
+    such."""
+    peak_hbm, peak_kind = measured_peak()
+    eff_gbs = BYTES_PER_UPDATE * updates_per_launch / launch_s / 1e9
+    wi = counters.get("warp_instructions_per_launch")
+    traffic = counters.get("dram_bytes_per_launch")
+    ipeak = issue_peak(clk)
+    out = {"bound": "alu", "limiter": "instruction issue (4 warp instructions per SM "
+                                      "per cycle)",
+           "achieved": wi / launch_s if wi else None, "peak": ipeak,
+           "unit": "warp instructions/s", "frac": (wi / launch_s / ipeak) if wi else None,
+           "traffic": traffic, "kernel": kernel_tag,
+           "launch_us": launch_s * 1e6, "cell_updates_per_launch": updates_per_launch,
+           "warp_instructions_per_launch": wi,
+           "counters": "profiles/traffic.txt (ncu, same kernel sources)" if wi else
+                       "no committed counters for the current kernel sources",
+           "peak_model": "4 issue slots per SM per cycle x SMs x sampled SM clock",
+           "effective_hbm": {"achieved_GBps": eff_gbs, "peak_GBps": peak_hbm,
+                             "peak_source": peak_kind,
+                             "effective_frac_of_hbm_peak": eff_gbs / peak_hbm,
+                             "bytes_model": "8 B per cell update (int32 read + write) x "
+                                            "cell updates per launch; not a bandwidth: "
+                                            "the state stays on chip for K steps"}}
+    if traffic:
+        dram_gbs = traffic / launch_s / 1e9
+        out["dram"] = {"GBps": dram_gbs, "frac_of_hbm_peak": dram_gbs / peak_hbm,
+                       "bytes_per_launch": traffic}
+    return out
 
 
 def fv_baselines(F, p, stream, torch):
@@ -397,7 +457,7 @@ def _timed(stream, torch, fn, reps):
     return statistics.median(ts)
 
 
-def other_workloads(F, torch, stream):
+def other_workloads(F, torch, stream, clk=None, finals=None):
     """The other workloads of the path, each timed on the device (median of
     5; the Sod runs, about 1.6 s each, once), with inputs resident on the GPU:
       - high-frequency transport, 2^24 cells, upwind nu = 0.9, 2000 steps
@@ -405,6 +465,7 @@ def other_workloads(F, torch, stream):
       - linear advection, 1024 cells, 2000 steps (a latency case);
       - Sod, 2^16 cells, componentwise-quantised Roe, to t = 0.2, and the
         FP64 Roe finite-volume baseline on the same grid."""
+    from paper_2604_06947_gb300 import build as B
     peak, _ = measured_peak()
     out = {}
     for name, make in (("high_frequency_16m", I.high_frequency_problem),
@@ -423,16 +484,27 @@ def other_workloads(F, torch, stream):
             run()
             t = _timed(stream, torch, run, 5)
         F.fqnm_sync(s.h)
+        launches = F.fqnm_get_stats(s.h)["launches"]      # stepping launches of one run
+        if finals is not None:
+            finals[name] = (p, s.state())
         rule = F.fqnm_get_rule(s.h)
         eff = BYTES_PER_UPDATE * p.n * p.steps / t / 1e9
         out[name] = {"n_cells": p.n, "time_steps": p.steps, "seconds": t,
                      "value": p.n * p.steps / t, "unit": UNIT,
-                     "effective_GBps": eff, "frac_of_hbm_peak": eff / peak,
+                     "effective_GBps": eff, "effective_frac_of_hbm_peak": eff / peak,
                      "map": "closed form %d/%d" % (rule["num"], rule["den"])
                      if rule["evaluator"] == 2 else "table",
                      "plan": dict({k: st[k] for k in ("layout", "cells_per_thread", "block", "k")},
                                   kernel={1: "k_step_naive", 2: "k_step_tb",
                                           4: "k_step_resident"}.get(st["kernel"], st["kernel"]))}
+        if name == "high_frequency_16m" and st["kernel"] == 2 and launches:
+            # the large line: its own roofline object (the state, 2 x 64 MiB,
+            # is about the L2's size, so HBM could bind here)
+            tag = "k_step_tb:L%d:V%d" % (st["layout"], st["cells_per_thread"])
+            c = profiled_counters(tag, B.kernel_digest(),
+                                  "upwind_closed_2^24_cells_K%d" % st["k"])
+            out[name]["roofline"] = stepping_roofline(c, p.n * p.steps / launches,
+                                                      t / launches, clk, tag)
         s.close()
     # Sod: integer Roe and the FP64 Roe FV baseline
     p = I.sod_problem(n=1 << 16)
@@ -446,6 +518,12 @@ def other_workloads(F, torch, stream):
                                                F.fqnm_step(s.h, p.steps)), 1)
     inv = F.fqnm_invariants(s.h)
     u = s.observe()
+    if finals is not None:
+        # the state after the first 2000 steps (parity) and the final density
+        # (its L1 error against the exact Riemann solution), both untimed
+        F.fqnm_load_field(s.h, U0, p.n, on_device=True)
+        F.fqnm_step(s.h, 2000)
+        finals["sod_65k"] = (p, s.state().reshape(3, -1), u[0].copy())
     s.close()
     fv = F.fqnm_fv_create(F.make_flux("euler_roe", gamma=p.gamma), p.dx, p.dt, "transmissive", 64)
     F.fqnm_fv_set_stream(fv, stream)
@@ -455,11 +533,15 @@ def other_workloads(F, torch, stream):
                                               F.fqnm_fv_step(fv, p.steps)), 1)
     ufv = F.fqnm_fv_observe(fv, p.n, 3)
     F.fqnm_fv_destroy(fv)
+    if finals is not None:
+        finals["sod_65k_fv64"] = ufv[0].copy()
     q0 = [int(round(v)) for v in (p.U0.sum(axis=1) / np.array(p.delta))]
     out["sod_65k"] = {
         "n_cells": p.n, "time_steps": p.steps, "t_end": 0.2,
         "seconds": t_int, "face_evaluations_per_s": (p.n + 1) * p.steps / t_int,
-        "fv64_roe_seconds": t_fv,
+        "fv64_roe_seconds": t_fv, "integer_speedup_vs_fv64": t_fv / t_int,
+        "l1_density_vs_exact": None,             # filled in by the CPU leg (exact Riemann)
+        "l1_density_fv64_vs_exact": None,
         "l1_density_integer_vs_fv64": float(p.dx * np.abs(u[0] - ufv[0]).sum()),
         "totals_balance_exact": all(inv["mass"][k] == q0[k] - inv["boundary_flux"][k]
                                     for k in range(3)),
@@ -600,12 +682,15 @@ def serving_block(torch):
     reqs = I.serving_stream()
     dev = S.DeviceStream(reqs)
     online = S.serve_batched(reqs, dev=dev, plan="autotune")
+    out_online = dev.out.clone()                 # the online pass's results, kept
     tuned = {k: online["plan"][k] for k in ("cells_per_thread", "block", "k", "layout")}
     offline_reqs = [I.ServeRequest(r.rid, 0.0, r.problem, r.data_seed) for r in reqs]
     offline = S.serve_batched(offline_reqs, dev=dev, plan=tuned)
     out_single = torch.empty_like(dev.out)
     one = S.serve_one_by_one(reqs, dev=dev, out=out_single)
-    identical = bool(torch.equal(out_single, dev.out))
+    online_identical = bool(torch.equal(out_single, out_online))
+    offline_identical = bool(torch.equal(out_single, dev.out))
+    dev.out.copy_(out_online)                    # the oracle check reads the online results
     keys = ("value", "p50_ms", "p99_ms", "max_ms")
     return {
         "workload": "4096 requests, Poisson 2000/s, half linear / half Burgers, "
@@ -617,8 +702,11 @@ def serving_block(torch):
         "batched_offline": {"value": offline["value"], "gpu_value": offline["value_gpu"],
                             "makespan_s": offline["makespan_s"]},
         "one_problem_at_a_time": dict({k: one[k] for k in keys}, busy_s=one["busy_s"]),
-        "results_identical": identical,
+        "online_identical_to_one_at_a_time": online_identical,
+        "offline_identical_to_one_at_a_time": offline_identical,
+        "results_identical": online_identical and offline_identical,
         "unit": UNIT,
+        "_dev": dev, "_reqs": reqs,
     }
 
 
@@ -646,42 +734,125 @@ def cpu_baseline(p, steps: int = CPU_SAMPLE_STEPS):
     from oracle import oracle as O
     q0 = O.quantise(p.u0, p.delta)
     t0 = time.perf_counter()
-    O.step(q0, p.flux, p.delta, p.dx, p.dt, steps, alpha=p.alpha)
+    q = O.step(q0, p.flux, p.delta, p.dx, p.dt, steps, alpha=p.alpha)
     dt = time.perf_counter() - t0
     return {"value": p.n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d cells x %d of the 10^4 time steps (same seeded problem), "
                       "single-threaded C oracle, %.1f s" % (p.n, steps, dt),
-            "host": host_cpu()}
+            "host": host_cpu(), "_q_sample": (steps, q)}
 
 
-def _oracle_request(rq):
-    """One serving request solved by the single-threaded oracle (a pool
-    worker): returns its cell updates and the seconds of its steps."""
+def oracle_parity(p, final_q, sample, finals) -> dict:
+    """The GPU's results against the oracle, element by element (untimed).
+
+    - the timed workload: the final state of the last timed bench step
+      (2^20 cells after 10^4 steps) against the oracle's, assembled from
+      dependency windows run in parallel host processes; and the state
+      after the CPU baseline's own sample of steps against that sample;
+    - the high-frequency line (2^24 cells, 2000 steps): the whole final
+      state, the same way;
+    - the serving stream's sampled requests (filled in by the serving leg)."""
+    import torch
     from oracle import oracle as O
+    from paper_2604_06947_gb300 import fqnm as F
+    out = {}
+    t0 = time.perf_counter()
+    q0 = O.quantise(p.u0, p.delta)
+    want = O.step_by_windows(q0, p.steps, p.flux, p.delta, p.dx, p.dt, alpha=p.alpha)
+    diff = int((final_q.astype(np.int64) != want).sum())
+    out["burgers_1m_10k_steps"] = {"cells": int(p.n), "time_steps": p.steps,
+                                   "cells_differing": diff, "equal": diff == 0,
+                                   "oracle": "full state from dependency windows, %d host "
+                                             "processes, %.1f s"
+                                             % (os.cpu_count() or 1,
+                                                time.perf_counter() - t0)}
+    steps, q_cpu = sample
+    s = F.Solver.for_problem(p)
+    s.load(F.fqnm_quantise(p.u0, p.delta)).step(steps)
+    diff = int((s.state().astype(np.int64) != q_cpu).sum())
+    s.close()
+    out["burgers_1m_cpu_sample"] = {"cells": int(p.n), "time_steps": steps,
+                                    "cells_differing": diff, "equal": diff == 0,
+                                    "oracle": "the CPU baseline's own single-threaded run"}
+    if "high_frequency_16m" in finals:
+        ph, qh = finals["high_frequency_16m"]
+        t0 = time.perf_counter()
+        want = O.step_by_windows(O.quantise(ph.u0, ph.delta), ph.steps, ph.flux, ph.delta,
+                                 ph.dx, ph.dt, a=ph.a)
+        diff = int((qh.astype(np.int64) != want).sum())
+        out["high_frequency_16m_2000_steps"] = {
+            "cells": int(ph.n), "time_steps": ph.steps, "cells_differing": diff,
+            "equal": diff == 0,
+            "oracle": "full state from dependency windows, %d host processes, %.1f s"
+                      % (os.cpu_count() or 1, time.perf_counter() - t0)}
+    if "sod_65k" in finals:
+        ps, q2000, _ = finals["sod_65k"]
+        q0s = np.stack([O.quantise(ps.U0[k], ps.delta[k]) for k in range(3)]).astype(np.int64)
+        want = O.euler_step_by_windows(q0s, 2000, ps.gamma, ps.delta, ps.dx, ps.dt)
+        diff = int((q2000 != want).any(axis=0).sum())
+        out["sod_65k_2000_steps"] = {"cells": int(ps.n), "time_steps": 2000,
+                                     "cells_differing": diff, "equal": diff == 0,
+                                     "oracle": "full state (rho, m, E) from dependency "
+                                               "windows"}
+    out["all_equal"] = all(v.get("equal", False) for v in out.values() if isinstance(v, dict))
+    return out
+
+
+def sod_accuracy(finals, workloads):
+    """L1 density error of the Sod runs against the exact Riemann solution
+    at t = 0.2 (the oracle's exact solver, sampled at the cell centres)."""
+    from oracle import oracle as O
+    if not workloads or "sod_65k" not in finals or "sod_65k" not in workloads:
+        return
+    p, _, rho = finals["sod_65k"]
+    x = I.cell_centres(p.n)
+    rex, _, _ = O.riemann_sample(p.gamma, I.SOD_LEFT, I.SOD_RIGHT, 0.5, I.SOD_T_END, x)
+    workloads["sod_65k"]["l1_density_vs_exact"] = float(p.dx * np.abs(rho - rex).sum())
+    if "sod_65k_fv64" in finals:
+        workloads["sod_65k"]["l1_density_fv64_vs_exact"] = float(
+            p.dx * np.abs(finals["sod_65k_fv64"] - rex).sum())
+
+
+def _oracle_request(job):
+    """One serving request solved by the single-threaded oracle (a pool
+    worker): returns its index, cell updates, the seconds of its steps and
+    its final state."""
+    from oracle import oracle as O
+    i, rq = job
     p = I.materialise(rq)
     q0 = O.quantise(p.u0, p.delta)
+    p.u0 = None
     t0 = time.perf_counter()
-    O.step(q0, p.flux, p.delta, p.dx, p.dt, p.steps, a=p.a, alpha=p.alpha)
-    return p.n * p.steps, time.perf_counter() - t0
+    q = O.step(q0, p.flux, p.delta, p.dx, p.dt, p.steps, a=p.a, alpha=p.alpha)
+    return i, p.n * p.steps, time.perf_counter() - t0, q
 
 
-def serving_cpu_baseline(every: int = 16):
+def serving_cpu_baseline(result_of, reqs, every: int = 16):
     """The serving stream's problems on the host cores: one single-threaded
     oracle instance per core (a spawned process pool), on every 16th request
-    of the 4096; value = their cell updates / the pool's wall time."""
+    of the 4096; value = their cell updates / the pool's wall time.  Each
+    oracle result is then compared, element by element, with the online
+    batched pass's result for that request (result_of(i), an int array)."""
     import multiprocessing as mp
-    reqs = I.serving_stream()[::every]
+    idx = list(range(0, len(reqs), every))
     cores = os.cpu_count() or 1
-    order = sorted(reqs, key=lambda r: -r.problem.n * r.problem.steps)   # longest first
+    order = sorted(idx, key=lambda i: -reqs[i].problem.n * reqs[i].problem.steps)
+    jobs = [(i, reqs[i]) for i in order]
     with mp.get_context("spawn").Pool(cores) as pool:
         t0 = time.perf_counter()
-        res = pool.map(_oracle_request, order, chunksize=1)
+        res = pool.map(_oracle_request, jobs, chunksize=1)
         wall = time.perf_counter() - t0
-    updates = sum(r[0] for r in res)
-    return {"value": updates / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+    updates = sum(r[1] for r in res)
+    equal = sum(int(np.array_equal(np.asarray(result_of(i), dtype=np.int64), q))
+                for i, _, _, q in res)
+    base = {"value": updates / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "every %dth request (%d of 4096, %.3g cell updates), one single-threaded "
                       "C oracle per core, %.1f s wall, %.1f core-s"
-                      % (every, len(reqs), updates, wall, sum(r[1] for r in res))}
+                      % (every, len(idx), updates, wall, sum(r[2] for r in res))}
+    check = {"requests_checked": len(res), "requests_equal": equal,
+             "equal": equal == len(res),
+             "compared": "online batched result vs the oracle, every %dth request" % every}
+    return base, check
 
 
 def run_reference(args):

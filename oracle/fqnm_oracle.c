@@ -325,6 +325,38 @@ int orc_cone(int kind, double a, double alpha, double delta, double dx,
     return 0;
 }
 
+/* Windowed parity, the same dependency argument for a run of cells: W
+ * consecutive cells after `steps` steps depend only on the window of
+ * W + 2*steps cells around them.  `window` holds that window of the initial
+ * state (len = W + 2*steps, periodic wrap already applied by the caller);
+ * each step evaluates eq. update_rule on the cells whose two faces lie in
+ * the window and drops the two outermost cells.  `out` receives the W
+ * cells.  This is orc_cone for W > 1. */
+int orc_window(int kind, double a, double alpha, double delta, double dx,
+               double dt, int rounding, const int64_t* window, int64_t len,
+               int64_t steps, int64_t* out)
+{
+    if (steps < 0 || len < 2 * steps + 1) return -1;
+    orc_maps M;
+    if (orc_maps_init(&M, kind, a, alpha, delta, dx, dt, rounding, window, len, 64))
+        return -1;
+    int64_t* w = (int64_t*)malloc(sizeof(int64_t) * (size_t)len);
+    int64_t* F = (int64_t*)malloc(sizeof(int64_t) * (size_t)len);
+    if (!w || !F) { free(w); free(F); orc_maps_free(&M); return -1; }
+    memcpy(w, window, sizeof(int64_t) * (size_t)len);
+    int64_t L = len;
+    for (int64_t s = 0; s < steps; s++) {
+        for (int64_t j = 0; j + 1 < L; j++)          /* F[j]: face between j, j+1 */
+            F[j] = orc_pp(&M, w[j]) + orc_pm(&M, w[j + 1]);
+        for (int64_t j = 1; j + 1 < L; j++)          /* cell j has faces j-1, j */
+            w[j - 1] = w[j] - (F[j] - F[j - 1]);
+        L -= 2;
+    }
+    memcpy(out, w, sizeof(int64_t) * (size_t)L);
+    free(w); free(F); orc_maps_free(&M);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Two-point transfer of eq. transfer_operator_equivalence_definition:       */
 /*   Phi(qL,qR) = round( F(delta qL, delta qR) * dt/dx * delta^-1 )          */
@@ -585,6 +617,63 @@ int orc_euler_roe_step(double g, const double* delta, double dx, double dt,
             if (bflux) bflux[k] += P[n] - P[0];
         }
     }
+    free(Phi);
+    return 0;
+}
+
+/* Windowed parity for the integer Euler step: after `steps` steps a cell
+ * depends only on the cells within `steps` of it (each face reads its two
+ * neighbours), or on the domain's edge cell through the transmissive ghost.
+ * `qw` is [3][len] SoA: cells [a, a+len) of a domain [0, n); left_end says
+ * a == 0 and right_end says a+len == n, where the ghost of
+ * orc_euler_roe_step applies.  Each step evaluates the faces whose two
+ * cells are known (plus the ghost faces at a domain end) and updates the
+ * cells that have both faces, so a side that is not a domain end loses one
+ * cell per step.  `out` ([3][W], W = len - steps*(2 - left_end - right_end))
+ * receives the surviving cells, which equal cells
+ * [a + (left_end ? 0 : steps), ...) of the full run. */
+int orc_euler_window(double g, const double* delta, double dx, double dt,
+                     int rounding, const int64_t* qw, int64_t len,
+                     int left_end, int right_end, int64_t steps, int64_t* out)
+{
+    int64_t shrink = (left_end ? 0 : 1) + (right_end ? 0 : 1);
+    if (steps < 0 || len < 1 || len - shrink * steps < 1) return -1;
+    double lambda = dt / dx;
+    int64_t* q = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)len);
+    int64_t* Phi = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)(len + 1));
+    if (!q || !Phi) { free(q); free(Phi); return -1; }
+    memcpy(q, qw, sizeof(int64_t) * 3 * (size_t)len);
+    int64_t lo = 0, hi = len - 1;                   /* cells still exact */
+    for (int64_t s = 0; s < steps; s++) {
+        /* face f sits between cells f-1 and f (f = lo..hi+1); the outer
+         * faces exist only at a domain end, against the ghost copy */
+        int64_t f0 = left_end ? lo : lo + 1, f1 = right_end ? hi + 1 : hi;
+        for (int64_t f = f0; f <= f1; f++) {
+            int64_t iL = f - 1 < lo ? lo : f - 1;
+            int64_t iR = f > hi ? hi : f;
+            double UL[3], UR[3], F[3];
+            for (int k = 0; k < 3; k++) {
+                UL[k] = delta[k] * (double)q[k * len + iL];
+                UR[k] = delta[k] * (double)q[k * len + iR];
+            }
+            orc_roe_flux(g, UL, UR, F);
+            for (int k = 0; k < 3; k++)
+                Phi[k * (len + 1) + f] =
+                    (int64_t)orc_round((F[k] * lambda) * (1.0 / delta[k]), rounding);
+        }
+        int64_t c0 = left_end ? lo : lo + 1, c1 = right_end ? hi : hi - 1;
+        for (int k = 0; k < 3; k++) {
+            int64_t* P = Phi + k * (len + 1);
+            for (int64_t i = c0; i <= c1; i++)
+                q[k * len + i] = q[k * len + i] - (P[i + 1] - P[i]);
+        }
+        lo = c0;
+        hi = c1;
+    }
+    int64_t W = hi - lo + 1;
+    for (int k = 0; k < 3; k++)
+        memcpy(out + k * W, q + k * len + lo, sizeof(int64_t) * (size_t)W);
+    free(q);
     free(Phi);
     return 0;
 }

@@ -68,6 +68,8 @@ def _declare(L):
     L.orc_step_split_faces.argtypes = [_i, _d, _d, _d, _d, _d, _i, _i, _i64p, _l, _l]
     L.orc_cone.argtypes = [_i, _d, _d, _d, _d, _d, _i, _i64p, _l, _l,
                            C.POINTER(C.c_int64)]
+    L.orc_window.argtypes = [_i, _d, _d, _d, _d, _d, _i, _i64p, _l, _l, _i64p]
+    L.orc_euler_window.argtypes = [_d, _f64p, _d, _d, _i, _i64p, _l, _i, _i, _l, _i64p]
     L.orc_two_point_phi.argtypes = [_i, _d, _d, _d, _d, _d, _i, _l, _l]
     L.orc_two_point_phi.restype = C.c_int64
     L.orc_step_two_point.argtypes = [_i, _d, _d, _d, _d, _d, _i, _i, _i64p, _l, _l]
@@ -87,7 +89,8 @@ def _declare(L):
     L.orc_riemann_right_shock_speed.argtypes = [_d] * 7
     L.orc_riemann_right_shock_speed.restype = _d
     for name in ("orc_quantise", "orc_split_table", "orc_step_split", "orc_step_nd",
-                 "orc_step_split_faces", "orc_cone", "orc_step_two_point",
+                 "orc_step_split_faces", "orc_cone", "orc_window", "orc_euler_window",
+                 "orc_step_two_point",
                  "orc_invariants", "orc_fv_step_f64", "orc_fv_step_f32",
                  "orc_euler_roe_step", "orc_euler_fv_step_f64", "orc_euler_roe_step_mask",
                  "orc_riemann_star", "orc_riemann_sample"):
@@ -162,6 +165,119 @@ def cone(q0, centre, steps, kind, delta, dx, dt, a=0.0, alpha=0.0,
                           ROUNDING[rounding], w, w.shape[0], steps,
                           C.byref(out)), "cone")
     return out.value
+
+
+def _scalar_window_cut(q0, first, count, steps):
+    n = q0.shape[0]
+    idx = np.arange(first - steps, first + count + steps) % n
+    return np.ascontiguousarray(np.asarray(q0, dtype=np.int64)[idx])
+
+
+def _scalar_window_run(w, steps, kind, delta, dx, dt, a, alpha, rounding):
+    out = np.empty(w.shape[0] - 2 * steps, dtype=np.int64)
+    _check(lib().orc_window(KINDS[kind], a, alpha, delta, dx, dt, ROUNDING[rounding],
+                            w, w.shape[0], steps, out), "window")
+    return out
+
+
+def window(q0, first, count, steps, kind, delta, dx, dt, a=0.0, alpha=0.0,
+           rounding="half_even"):
+    """Cells [first, first+count) (mod n) after `steps` periodic steps,
+    from their dependency window of count + 2*steps cells only."""
+    w = _scalar_window_cut(q0, first, count, steps)
+    return _scalar_window_run(w, steps, kind, delta, dx, dt, a, alpha, rounding)
+
+
+def _euler_window_cut(q0, first, count, steps):
+    n = q0.shape[1]
+    a = max(0, first - steps)
+    b = min(n, first + count + steps)
+    w = np.ascontiguousarray(np.asarray(q0, dtype=np.int64)[:, a:b])
+    left, right = int(a == 0), int(b == n)
+    lo = first - (a if left else a + steps)        # offset of `first` in the result
+    return w, left, right, lo
+
+
+def _euler_window_run(w, left, right, lo, count, steps, gamma, delta, dx, dt, rounding):
+    L = w.shape[1]
+    W = L - steps * (2 - left - right)
+    out = np.empty((3, W), dtype=np.int64)
+    _check(lib().orc_euler_window(gamma, np.asarray(delta, dtype=np.float64), dx, dt,
+                                  ROUNDING[rounding], w.reshape(-1), L, left, right,
+                                  steps, out.reshape(-1)), "euler_window")
+    return np.ascontiguousarray(out[:, lo:lo + count])
+
+
+def euler_window(q0, first, count, steps, gamma, delta, dx, dt, rounding="half_even"):
+    """Cells [first, first+count) of the integer Euler state (3, n) after
+    `steps` transmissive steps, from their dependency window only (clipped
+    at the domain ends, where the ghost copy applies)."""
+    w, left, right, lo = _euler_window_cut(q0, first, count, steps)
+    return _euler_window_run(w, left, right, lo, count, steps, gamma, delta, dx, dt,
+                             rounding)
+
+
+def _window_job(job):
+    kind, args = job
+    if kind == "scalar":
+        return _scalar_window_run(*args)
+    return _euler_window_run(*args)
+
+
+def _split(n, parts):
+    edges = np.linspace(0, n, parts + 1).astype(np.int64)
+    return [(int(a), int(b - a)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+
+def _pool_map(jobs, procs):
+    """Run window jobs in a spawned process pool (safe in a process that
+    already holds a CUDA context: spawn starts fresh interpreters)."""
+    import multiprocessing as mp
+    import sys
+    procs = max(1, min(procs or os.cpu_count() or 1, len(jobs)))
+    main_file = getattr(sys.modules.get("__main__"), "__file__", None)
+    if procs == 1 or not (main_file and os.path.exists(main_file)):
+        # a spawned worker re-imports the main script; without one (an
+        # interactive or stdin session) run the windows in this process
+        return [_window_job(j) for j in jobs]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_window_job, jobs, chunksize=1)
+
+
+def step_by_windows(q0, steps, kind, delta, dx, dt, a=0.0, alpha=0.0,
+                    rounding="half_even", parts=0, procs=0):
+    """The whole periodic state after `steps` steps, assembled from
+    independent windows evaluated in parallel processes (each window is
+    the plain cell form of eq. update_rule on its dependency window; see
+    window()).  Same result as step(), bit for bit."""
+    q0 = np.asarray(q0, dtype=np.int64)
+    parts = parts or (os.cpu_count() or 1)
+    jobs = [("scalar", (_scalar_window_cut(q0, f, c, steps), steps, kind, delta, dx, dt,
+                        a, alpha, rounding))
+            for f, c in _split(q0.shape[0], parts)]
+    return np.concatenate(_pool_map(jobs, procs))
+
+
+def euler_cells(q0, spans, steps, gamma, delta, dx, dt, rounding="half_even", procs=0):
+    """The integer Euler state on the cell runs `spans` [(first, count), ...]
+    after `steps` steps, each from its dependency window, in parallel
+    processes.  Returns a list of (3, count) arrays."""
+    q0 = np.asarray(q0, dtype=np.int64)
+    jobs = []
+    for f, c in spans:
+        w, left, right, lo = _euler_window_cut(q0, f, c, steps)
+        jobs.append(("euler", (w, left, right, lo, c, steps, gamma, delta, dx, dt, rounding)))
+    return _pool_map(jobs, procs)
+
+
+def euler_step_by_windows(q0, steps, gamma, delta, dx, dt, rounding="half_even",
+                          parts=0, procs=0):
+    """The whole Euler state after `steps` steps from parallel windows;
+    equal to euler_step()'s state, bit for bit."""
+    parts = parts or (os.cpu_count() or 1)
+    spans = _split(np.asarray(q0).shape[1], parts)
+    return np.concatenate(euler_cells(q0, spans, steps, gamma, delta, dx, dt, rounding,
+                                      procs), axis=1)
 
 
 def two_point_phi(kind, delta, dx, dt, qL, qR, a=0.0, alpha=0.0,

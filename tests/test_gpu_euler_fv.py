@@ -14,7 +14,13 @@ G = I.SOD_GAMMA
 
 
 def sod_q0(p):
-    return np.stack([F.fqnm_quantise(p.U0[k], p.delta[k], state_bits=64) for k in range(3)])
+    """The initial state (3, n): the GPU's quantisation, checked equal to the
+    oracle's, which both sides then start from."""
+    from oracle import oracle as O
+    want = np.stack([O.quantise(p.U0[k], p.delta[k]) for k in range(3)]).astype(np.int64)
+    got = np.stack([F.fqnm_quantise(p.U0[k], p.delta[k], state_bits=64) for k in range(3)])
+    assert np.array_equal(got, want)
+    return want
 
 
 def euler_solver(p):
@@ -84,6 +90,48 @@ def test_sod_large_grids_first_steps_bit_exact(orc, n, checkpoints):
         assert np.array_equal(s.state(), q), c
     assert s.invariants()["boundary_flux"] == list(bf_total)
     s.close()
+
+
+@pytest.mark.parametrize("n", [1 << 20, 1 << 22])
+def test_sod_large_grids_2000_steps_full_state(orc, n):
+    """The two large Sod grids after 2000 steps: every integer state of the
+    whole tube equal to the oracle's, which is assembled from dependency
+    windows evaluated in parallel host processes (each window runs the
+    plain componentwise Roe transfer with the transmissive ghost at a tube
+    end)."""
+    p = I.sod_problem(n=n)
+    q0 = sod_q0(p)
+    s = euler_solver(p).load(q0)
+    s.step(2000)
+    got = s.state().reshape(3, -1)
+    s.close()
+    want = orc.euler_step_by_windows(q0, 2000, p.gamma, p.delta, p.dx, p.dt)
+    bad = np.flatnonzero((got != want).any(axis=0))
+    assert bad.size == 0, (bad.size, bad[:8])
+    assert not np.array_equal(got, q0)
+
+
+def test_sod_1m_10k_steps_wave_region(orc):
+    """2^20 cells after 10^4 steps: the whole region the waves have reached
+    (every cell within 10^4 cells of the diaphragm) and both tube ends
+    equal to the oracle's cells, from dependency windows."""
+    p = I.sod_problem(n=1 << 20)
+    steps = 10_000
+    q0 = sod_q0(p)
+    s = euler_solver(p).load(q0)
+    s.step(steps)
+    got = s.state().reshape(3, -1)
+    s.close()
+    mid = p.n // 2
+    spans = [(mid - steps + k * (2 * steps) // 16, (2 * steps) // 16) for k in range(16)]
+    spans += [(0, 256), (p.n - 256, 256)]
+    for (f, c), want in zip(spans, orc.euler_cells(q0, spans, steps, p.gamma, p.delta,
+                                                   p.dx, p.dt)):
+        assert np.array_equal(got[:, f:f + c], want), (f, c)
+    # beyond the diaphragm's dependency cone the data were constant, so the
+    # state there is the initial one
+    outside = np.r_[0:mid - steps, mid + steps:p.n]
+    assert np.array_equal(got[:, outside], q0[:, outside])
 
 
 def test_sod_1m_long_run_conservation_and_density_error(orc):

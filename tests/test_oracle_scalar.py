@@ -285,6 +285,30 @@ def test_cone_matches_full_run(orc):
                         alpha=p.alpha) == full[i]
 
 
+@pytest.mark.parametrize("kind,a,alpha,make", [
+    ("burgers_lf", 0.0, None, lambda: I.burgers_problem(n=2048, steps=0)),
+    ("linear_upwind", 1.0, 0.0, lambda: I.high_frequency_problem(n=2048)),
+])
+def test_window_matches_full_run(orc, kind, a, alpha, make):
+    """A run of cells from its dependency window alone equals those cells of
+    the full periodic run, including runs that wrap around the line and a
+    window wider than the line; the state assembled from windows in
+    parallel processes equals the full run."""
+    p = make()
+    alpha = p.alpha if alpha is None else alpha
+    q0 = orc.quantise(p.u0, p.delta)
+    steps = 300
+    full = orc.step(q0, kind, p.delta, p.dx, p.dt, steps, a=a, alpha=alpha)
+    for first, count in ((0, 1), (0, 2048), (2000, 100), (1500, 37), (2047, 1), (700, 1300)):
+        got = orc.window(q0, first, count, steps, kind, p.delta, p.dx, p.dt, a=a, alpha=alpha)
+        assert np.array_equal(got, full[np.arange(first, first + count) % p.n]), (first, count)
+    assert orc.cone(q0, 5, steps, kind, p.delta, p.dx, p.dt, a=a, alpha=alpha) == full[5]
+    for parts, procs in ((5, 1), (3, 3)):
+        got = orc.step_by_windows(q0, steps, kind, p.delta, p.dx, p.dt, a=a, alpha=alpha,
+                                  parts=parts, procs=procs)
+        assert np.array_equal(got, full), (parts, procs)
+
+
 # ---------------------------------------------------------------------------
 # Theorem (transfer-operator equivalence) and its remark on collapse
 # ---------------------------------------------------------------------------
