@@ -184,12 +184,22 @@ typedef enum {
                                 step per launch.  3-D grids take K steps per launch (K in 1..4,
                                 default 2) by blocks of rows walking z; FQNM_OPT_KERNEL = 1
                                 selects one step per launch there too. */,
-    FQNM_OPT_VERIFY = 14     /* 1: at each synchronising call, check that every integer
+    FQNM_OPT_VERIFY = 14,    /* 1: at each synchronising call, check that every integer
                                 variable's total plus its counted boundary transfer still
                                 equals its value at load (eq. exact_conservation holds for
                                 every step, so a difference means the state was changed
                                 outside the steps); FQNM_ERR_STATE if not.  One reduction per
                                 sync.  Default 0. */
+    FQNM_OPT_FP64 = 15       /* EULER_ROE: which IEEE double steps of the integer Roe step
+                                run on the integer pipes instead of the FP64 unit (same
+                                results bit for bit; the GB300's FP64 unit executes 2
+                                operations per SM per cycle).  0: none; 1: the state's
+                                conversion delta*q and the transfer's scaling and rounding;
+                                2 (default): also every division and square root of the
+                                Roe flux, correctly rounded from an FP32 seed, Newton steps
+                                in 64-bit fixed point and an exact integer remainder (the
+                                FP64 instruction takes over for operands outside that
+                                path: zeros, subnormals, infinities, NaN). */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 
@@ -282,6 +292,25 @@ fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
 fqnm_status fqnm_invariants_noalloc(const int32_t* q, const int32_t* other,
                                     size_t n, int boundary, int64_t* out,
                                     void* stream);
+
+/* Diagnostics for FQNM_OPT_FP64 (the paper has no counterpart: these are the
+ * GB300 execution strategy's own checks).  Evaluates, elementwise on device
+ * arrays a, b of n doubles, an IEEE double step as the integer Roe step forms
+ * it on the integer pipes and as the FP64 instruction forms it:
+ *   op 0: a / b (round to nearest even)      op 1: sqrt(a)
+ *   op 2: (double)q * 2^e, q = the bits of a as int64, e = (int)b
+ *   op 3: R(a * 2^e) as int64 with `rounding`, e = (int)b (0 when NaN,
+ *         infinite or |R| >= 4e18)
+ * out_int / out_fp64: n int64 (the result's bits for ops 0-2, the integer
+ * for op 3), the integer-pipe result and the FP64 instruction's; out_path: n
+ * int32, bit 0 set when the integer path applied (ops 0, 1: otherwise the
+ * FP64 instruction's value is taken), for op 3 bit 1 / bit 2 the out-of-range
+ * flag of either side.  Device pointers, caller-owned; asynchronous on
+ * `stream` (NULL: the legacy default stream).  FQNM_ERR_ARG for op or
+ * rounding out of range or a null pointer. */
+fqnm_status fqnm_fp64_check(int op, int rounding, const double* a, const double* b,
+                            size_t n, int64_t* out_int, int64_t* out_fp64,
+                            int32_t* out_path, void* stream);
 
 /* ---- Level statistics (Supplementary Information, Entropy and Statistical
  * Structure) ------------------------------------------------------------------

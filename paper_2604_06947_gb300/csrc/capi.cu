@@ -166,6 +166,7 @@ struct fqnm_solver {
     int64_t margin = 1024;
     int closed_form = 1, recover = 1, autotune = 0, use_graph = 1;
     int qmask = 7;                          // Euler: components evolved as integers
+    int fp64_mode = 2;                      // Euler: FP64 steps on the integer pipes
     NdGrid grid{1, {0, 1, 1}};              // d > 1: the Cartesian step of Theorem (extension)
     int opt_nd_tile = 0;                    // 2-D tile shape (0: default)
     int nd_tuned_tile = -1, nd_tuned_k = 0; // d-D plan kept by the autotuner (-1: none)
@@ -500,6 +501,9 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_PDL:
         if (value < 0 || value > 1) return set_error(FQNM_ERR_ARG, "pdl must be 0 or 1");
         s->opt_pdl = (int)value; break;
+    case FQNM_OPT_FP64:
+        if (value < 0 || value > 2) return set_error(FQNM_ERR_ARG, "fp64 mode must be 0..2");
+        s->fp64_mode = (int)value; break;
     default: return set_error(FQNM_ERR_ARG, "unknown option %d", option);
     }
     if (s->loaded && s->nvars == 1 && option <= FQNM_OPT_K) {
@@ -1231,8 +1235,8 @@ static fqnm_status step_euler(fqnm_solver* s, uint64_t k)
     for (uint64_t i = 0; i < k; ++i) {
         CK(launch_euler_step((int64_t*)s->q[s->cur], (int64_t*)s->q[1 - s->cur],
                              (int64_t)s->n, s->flux.gamma, s->delta, s->lambda,
-                             s->flux.rounding, s->qmask, s->d_err, s->d_acc + ACC_BFLUX,
-                             s->stream));
+                             s->flux.rounding, s->qmask, s->fp64_mode, s->d_err,
+                             s->d_acc + ACC_BFLUX, s->stream));
         s->cur = 1 - s->cur;
         s->launches += 1;
     }

@@ -143,8 +143,8 @@ cudaError_t launch_observe_i64(const int64_t* q, int64_t n, double delta,
 // the bits of a double and take the floating-point update with the same flux
 cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
                               double gamma, const double* delta,
-                              double lambda, int rounding, int mask, unsigned* err,
-                              long long* bflux, cudaStream_t st);
+                              double lambda, int rounding, int mask, int fp64_mode,
+                              unsigned* err, long long* bflux, cudaStream_t st);
 
 // ---- k_fv.cu ----------------------------------------------------------------
 cudaError_t launch_fv_step_f64(int kind, double a, double alpha, double lambda,

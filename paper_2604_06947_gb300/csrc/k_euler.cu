@@ -10,17 +10,39 @@
 // boundary transfers are accumulated exactly in int64 so that
 // sum q^k(now) = sum q^k(load) - bflux^k.
 #include "fqnm_internal.h"
+#include "fp64_int.cuh"
+
+#include <cmath>
 #include "roe.cuh"
 
 namespace fqnm {
 
 namespace {
 
+// The Roe flux's arithmetic with division and square root on the integer
+// pipes (fp64_int.cuh; the FP64 instruction for operands outside that path).
+struct ArIntDivSqrt : Ar<double> {
+    static __device__ __forceinline__ double div(double a, double b)
+    {
+        bool ok;
+        const double r = f64i::div_rn(a, b, ok);
+        return ok ? r : __ddiv_rn(a, b);
+    }
+    static __device__ __forceinline__ double sqrt_(double a)
+    {
+        bool ok;
+        const double r = f64i::sqrt_rn(a, ok);
+        return ok ? r : __dsqrt_rn(a);
+    }
+};
+
 struct EulerParams {
     double g, lambda;
     double delta[3], inv_delta[3];
+    int edelta[3];              // delta_k = 2^edelta[k]
     int rounding;
     int mask;                   // components evolved as integers (1 rho, 2 m, 4 E)
+    int int_conv;               // conversions and rounding on the integer pipes
 };
 
 __device__ __forceinline__ double round_mode(double v, int mode)
@@ -31,19 +53,24 @@ __device__ __forceinline__ double round_mode(double v, int mode)
 }
 
 // A component in the mask holds an integer state (value delta*q); one outside
-// it holds the bits of its double value.
+// it holds the bits of its double value.  delta*q is formed on the integer
+// pipes (the same double as the FP64 conversion and scaling: delta is a
+// power of two) unless delta's exponent is out of that path's range.
 __device__ __forceinline__ double comp_value(const int64_t* __restrict__ q, long long n,
                                              long long i, int k, const EulerParams& P)
 {
     const long long v = q[k * n + i];
-    return ((P.mask >> k) & 1) ? __dmul_rn(P.delta[k], (double)v) : __longlong_as_double(v);
+    if (!((P.mask >> k) & 1)) return __longlong_as_double(v);
+    return P.int_conv ? f64i::i64_scaled_to_f64(v, P.edelta[k])
+                      : __dmul_rn(P.delta[k], (double)v);
 }
 
+template <class A>
 __device__ __forceinline__ RoeCell<double> load_cell(const int64_t* __restrict__ q, long long n,
                                                     long long i, const EulerParams& P)
 {
-    return roe_cell<double>(P.g, comp_value(q, n, i, 0, P), comp_value(q, n, i, 1, P),
-                            comp_value(q, n, i, 2, P));
+    return roe_cell<double, A>(P.g, comp_value(q, n, i, 0, P), comp_value(q, n, i, 1, P),
+                               comp_value(q, n, i, 2, P));
 }
 
 __device__ __forceinline__ RoeCell<double> shfl_cell(const RoeCell<double>& c, int src_delta, bool down)
@@ -57,14 +84,22 @@ __device__ __forceinline__ RoeCell<double> shfl_cell(const RoeCell<double>& c, i
 
 // The Roe flux of one face and, for the integer components, its quantised
 // transfer round(F lambda / delta).
+template <class A>
 __device__ __forceinline__ void transfer(const RoeCell<double>& L, const RoeCell<double>& R,
                                          const EulerParams& P, long long* Phi, double* F,
                                          unsigned* err)
 {
-    roe_flux_cells<double>(P.g, L, R, F);
+    roe_flux_cells<double, A>(P.g, L, R, F);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (!((P.mask >> k) & 1)) { Phi[k] = 0; continue; }
+        if (P.int_conv) {        // R(F lambda 2^-e): the scaling and rounding as integers
+            bool bad = false;
+            Phi[k] = f64i::f64_scaled_round_to_i64(__dmul_rn(F[k], P.lambda), -P.edelta[k],
+                                                   P.rounding, bad);
+            if (bad) atomicOr(err, ERRBIT_OVERFLOW);  // also NaN (negative pressure)
+            continue;
+        }
         double r = round_mode(__dmul_rn(__dmul_rn(F[k], P.lambda), P.inv_delta[k]), P.rounding);
         if (!(fabs(r) < 4.0e18)) {                 // also NaN (negative pressure)
             atomicOr(err, ERRBIT_OVERFLOW);
@@ -84,6 +119,7 @@ constexpr int EULER_OWN = 30;
 // transmissive ghost copy) and forms its quantities once; it evaluates the
 // face to its right with its right neighbour's quantities by shuffle, and
 // lanes 1..30 update their cells with the faces of lanes l-1 and l.
+template <class A>
 __global__ void k_euler_step(const int64_t* __restrict__ qin,
                              int64_t* __restrict__ qout, long long n,
                              EulerParams P, unsigned* err, long long* bflux)
@@ -92,11 +128,11 @@ __global__ void k_euler_step(const int64_t* __restrict__ qin,
     const int lane = threadIdx.x & 31;
     const long long c = warp * EULER_OWN - 1 + lane;
     const long long j = c < 0 ? 0 : (c >= n ? n - 1 : c);
-    const RoeCell<double> me = load_cell(qin, n, j, P);
+    const RoeCell<double> me = load_cell<A>(qin, n, j, P);
     const RoeCell<double> right = shfl_cell(me, 1, true);   // lane 31: unused face
     long long Fr[3], Fl[3];
     double Dr[3], Dl[3];
-    transfer(me, right, P, Fr, Dr, err);
+    transfer<A>(me, right, P, Fr, Dr, err);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
@@ -127,16 +163,21 @@ __global__ void k_euler_step(const int64_t* __restrict__ qin,
 
 cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
                               double gamma, const double* delta, double lambda,
-                              int rounding, int mask, unsigned* err, long long* bflux,
-                              cudaStream_t st)
+                              int rounding, int mask, int fp64_mode, unsigned* err,
+                              long long* bflux, cudaStream_t st)
 {
     EulerParams P;
     P.mask = mask;
     P.g = gamma;
     P.lambda = lambda;
+    P.int_conv = fp64_mode >= 1;
     for (int k = 0; k < 3; ++k) {
         P.delta[k] = delta[k];
         P.inv_delta[k] = 1.0 / delta[k];
+        P.edelta[k] = ilogb(delta[k]);
+        if (std::ldexp(1.0, P.edelta[k]) != delta[k] || P.edelta[k] < -1022 ||
+            P.edelta[k] > 960)
+            P.int_conv = 0;          // not a power of two in the integer path's range
     }
     P.rounding = rounding;
     // one warp per block: the warps (segments of 30 cells) then spread over
@@ -146,7 +187,10 @@ cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
     const int block = 32;
     const long long warps = (n + EULER_OWN - 1) / EULER_OWN;
     const long long grid = (warps * 32 + block - 1) / block;
-    k_euler_step<<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);
+    if (fp64_mode >= 2)
+        k_euler_step<ArIntDivSqrt><<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);
+    else
+        k_euler_step<Ar<double>><<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);
     note_launches();
     return cudaGetLastError();
 }

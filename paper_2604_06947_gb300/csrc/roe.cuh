@@ -45,10 +45,11 @@ struct RoeCell {
     T rho, m, E, u, p, H, s;
 };
 
-template <typename T>
+// A: the arithmetic (Ar<T>, or a policy with the same members that forms
+// some operations another way but with the same IEEE results).
+template <typename T, class A = Ar<T>>
 __device__ __forceinline__ RoeCell<T> roe_cell(T g, T rho, T m, T E)
 {
-    using A = Ar<T>;
     const T gm1 = A::sub(g, T(1)), half = T(0.5);
     RoeCell<T> c;
     c.rho = rho;
@@ -64,10 +65,9 @@ __device__ __forceinline__ RoeCell<T> roe_cell(T g, T rho, T m, T E)
 
 // The Roe flux between two cells whose quantities are already formed (the
 // same operations, in the same order, as roe_flux below).
-template <typename T>
+template <typename T, class A = Ar<T>>
 __device__ __forceinline__ void roe_flux_cells(T g, const RoeCell<T>& L, const RoeCell<T>& R, T* F)
 {
-    using A = Ar<T>;
     const T one = T(1), half = T(0.5), gm1 = A::sub(g, one);
     const T rhoL = L.rho, mL = L.m, EL = L.E, uL = L.u, pL = L.p, HL = L.H, sL = L.s;
     const T rhoR = R.rho, mR = R.m, ER = R.E, uR = R.u, pR = R.p, HR = R.H, sR = R.s;

@@ -30,7 +30,8 @@ ROUNDING = {"half_even": 0, "half_away": 1, "floor": 2}
 BOUNDARY = {"periodic": 0, "transmissive": 1}
 OPTION = {"kernel": 0, "layout": 1, "cells_per_thread": 2, "block": 3, "k": 4,
           "margin": 5, "closed_form": 6, "recover": 7, "autotune": 8, "graph": 9,
-          "pdl": 10, "pack16": 11, "quantise_mask": 12, "nd_tile": 13, "verify": 14}
+          "pdl": 10, "pack16": 11, "quantise_mask": 12, "nd_tile": 13, "verify": 14,
+          "fp64": 15}
 
 
 class FqnmError(RuntimeError):
@@ -106,6 +107,7 @@ PROTOTYPES = {
     "fqnm_invariants": (_st, [_vp, _vp, C.POINTER(fqnm_invariants_t)]),
     "fqnm_invariants_noalloc": (_st, [_vp, _vp, C.c_size_t, C.c_int,
                                       C.POINTER(C.c_int64), _vp]),
+    "fqnm_fp64_check": (_st, [C.c_int, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp, _vp, _vp]),
     "fqnm_get_size": (_st, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "fqnm_set_grid": (_st, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
     "fqnm_resume": (_st, [_vp, _vp, C.c_size_t, C.c_uint64, C.POINTER(C.c_int64)]),
@@ -362,6 +364,16 @@ def fqnm_invariants_noalloc(q_dev, n: int, other_dev=None, boundary: str = "peri
     _check(load().fqnm_invariants_noalloc(_dptr(q_dev), _dptr(other_dev) or None, n,
                                           BOUNDARY[boundary], out, _stream(stream)))
     return out[0], out[1], out[2]
+
+
+def fqnm_fp64_check(op: int, a_dev, b_dev, n: int, out_int, out_fp64, out_path,
+                    rounding: str = "half_even", stream=None):
+    """The integer-pipe IEEE double step `op` (0 divide, 1 square root,
+    2 scaled int64 conversion, 3 scaled rounding to int64) next to the FP64
+    instruction, on device arrays (see include/fqnm.h)."""
+    _check(load().fqnm_fp64_check(int(op), ROUNDING[rounding], _dptr(a_dev), _dptr(b_dev), n,
+                                  _dptr(out_int), _dptr(out_fp64), _dptr(out_path),
+                                  _stream(stream)))
 
 
 def fqnm_resume(h: int, q, step: int, boundary_flux=None, nvars: Optional[int] = None):
