@@ -197,9 +197,11 @@ typedef enum {
                                 conversion delta*q and the transfer's scaling and rounding;
                                 2 (default): also every division and square root of the
                                 Roe flux, correctly rounded from an FP32 seed, Newton steps
-                                in 64-bit fixed point and an exact integer remainder (the
-                                FP64 instruction takes over for operands outside that
-                                path: zeros, subnormals, infinities, NaN). */
+                                in 64-bit fixed point and an exact integer remainder, and
+                                its exact halvings and doublings on the exponent field;
+                                3: also the products of the wave strengths with the
+                                eigenvectors (the FP64 instruction takes over for operands
+                                outside these paths: subnormals, infinities, NaN). */
 } fqnm_option;
 fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value);
 
@@ -301,9 +303,11 @@ fqnm_status fqnm_invariants_noalloc(const int32_t* q, const int32_t* other,
  *   op 2: (double)q * 2^e, q = the bits of a as int64, e = (int)b
  *   op 3: R(a * 2^e) as int64 with `rounding`, e = (int)b (0 when NaN,
  *         infinite or |R| >= 4e18)
+ *   op 4: a * 2^k, k = (int)b in {-1, 1} (the exact halving and doubling)
+ *   op 5: a * b (round to nearest even)
  * out_int / out_fp64: n int64 (the result's bits for ops 0-2, the integer
  * for op 3), the integer-pipe result and the FP64 instruction's; out_path: n
- * int32, bit 0 set when the integer path applied (ops 0, 1: otherwise the
+ * int32, bit 0 set when the integer path applied (ops 0, 1, 4, 5: otherwise the
  * FP64 instruction's value is taken), for op 3 bit 1 / bit 2 the out-of-range
  * flag of either side.  Device pointers, caller-owned; asynchronous on
  * `stream` (NULL: the legacy default stream).  FQNM_ERR_ARG for op or

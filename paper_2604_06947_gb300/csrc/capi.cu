@@ -502,7 +502,7 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
         if (value < 0 || value > 1) return set_error(FQNM_ERR_ARG, "pdl must be 0 or 1");
         s->opt_pdl = (int)value; break;
     case FQNM_OPT_FP64:
-        if (value < 0 || value > 2) return set_error(FQNM_ERR_ARG, "fp64 mode must be 0..2");
+        if (value < 0 || value > 3) return set_error(FQNM_ERR_ARG, "fp64 mode must be 0..3");
         s->fp64_mode = (int)value; break;
     default: return set_error(FQNM_ERR_ARG, "unknown option %d", option);
     }

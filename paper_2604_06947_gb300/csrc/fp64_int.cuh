@@ -75,6 +75,52 @@ __device__ __forceinline__ long long f64_scaled_round_to_i64(double y, int s, in
     return neg ? -(long long)r : (long long)r;
 }
 
+// x * 2^k for k = +-1 on the exponent field (exact): ok = false when x is
+// subnormal or the result would leave the normal range (zero stays zero).
+__device__ __forceinline__ double scale2_rn(double x, int k, bool& ok)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7ff);
+    const bool zero = (b << 1) == 0;
+    ok = zero || (E >= 1 && E <= 2046 && E + k >= 1 && E + k <= 2046);
+    return zero ? x : __longlong_as_double((long long)(b + ((long long)k << 52)));
+}
+
+// a * b rounded to nearest even on the integer pipes: the 106-bit product of
+// the two 53-bit significands from four 32 x 32 -> 64-bit multiplies, then
+// normalisation by one bit and rounding on the discarded bits.  ok = false
+// (use the FP64 instruction) for subnormal, infinite or NaN operands and
+// for products near the ends of the exponent range; a zero times a finite
+// number is handled here.
+__device__ __forceinline__ double mul_rn(double a, double b, bool& ok)
+{
+    const unsigned long long ab = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
+    const int Ea = (int)((ab >> 52) & 0x7ff), Eb = (int)((bb >> 52) & 0x7ff);
+    const unsigned long long sgn = (ab ^ bb) & SIGN;
+    const bool zero = (ab << 1) == 0 || (bb << 1) == 0;
+    const int Er0 = Ea + Eb - 1023;               // before the normalisation bit
+    ok = zero ? (Ea != 0x7ff && Eb != 0x7ff)
+              : (Ea >= 1 && Ea <= 2046 && Eb >= 1 && Eb <= 2046 && Er0 >= 1 && Er0 <= 2044);
+    const unsigned long long ma = (ab & FRAC) | HIDDEN, mb = (bb & FRAC) | HIDDEN;
+    const unsigned a0 = (unsigned)ma, a1 = (unsigned)(ma >> 32);
+    const unsigned b0 = (unsigned)mb, b1 = (unsigned)(mb >> 32);
+    const unsigned long long p00 = (unsigned long long)a0 * b0;
+    unsigned long long mid = (unsigned long long)a1 * b0 + (p00 >> 32);
+    mid += (unsigned long long)a0 * b1;
+    const unsigned long long hi = (unsigned long long)a1 * b1 + (mid >> 32);  // bits 64..105
+    const unsigned long long lo = (mid << 32) | (p00 & 0xffffffffull);        // bits 0..63
+    // product in [2^104, 2^106): keep 53 bits from bit 52 + nrm
+    const int nrm = (int)(hi >> 41);
+    const int sh = 52 + nrm;
+    unsigned long long mant = (hi << (64 - sh)) | (lo >> sh);
+    const bool rb = (lo >> (sh - 1)) & 1ull;
+    const bool sticky = (lo << (65 - sh)) != 0;
+    mant += (rb && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+    const unsigned long long bits = sgn | (((unsigned long long)(Er0 + nrm - 1) << 52) + mant);
+    return __longlong_as_double((long long)(zero ? sgn : bits));
+}
+
 // ---------------------------------------------------------------------------
 // Correctly rounded division and square root (round to nearest, ties to
 // even) on the integer pipes.

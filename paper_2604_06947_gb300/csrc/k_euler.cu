@@ -19,20 +19,73 @@ namespace fqnm {
 
 namespace {
 
+// The FP64 instructions for operands outside the integer paths, as calls:
+// inlined, their code was scheduled into the common path and executed
+// whether or not a lane needed it (2^20-cell Sod step: 5.7 s against 3.8 s
+// for 20,000 steps), while a call runs only when taken.
+__device__ __noinline__ double fp64_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __noinline__ double fp64_sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __noinline__ double fp64_mul(double a, double b) { return __dmul_rn(a, b); }
+
 // The Roe flux's arithmetic with division and square root on the integer
 // pipes (fp64_int.cuh; the FP64 instruction for operands outside that path).
 struct ArIntDivSqrt : Ar<double> {
+    // The kernel's lanes run these in step (no lane-dependent branch around
+    // the flux), so the FP64 call is a warp-uniform branch taken only when
+    // some lane's operands fall outside the integer path.
     static __device__ __forceinline__ double div(double a, double b)
     {
         bool ok;
-        const double r = f64i::div_rn(a, b, ok);
-        return ok ? r : __ddiv_rn(a, b);
+        double r = f64i::div_rn(a, b, ok);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (!ok) r = fp64_div(a, b);
+        }
+        return r;
     }
     static __device__ __forceinline__ double sqrt_(double a)
     {
         bool ok;
-        const double r = f64i::sqrt_rn(a, ok);
-        return ok ? r : __dsqrt_rn(a);
+        double r = f64i::sqrt_rn(a, ok);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (!ok) r = fp64_sqrt(a);
+        }
+        return r;
+    }
+    // |a|: clear the sign bit (an integer operation; no FP64 instruction)
+    static __device__ __forceinline__ double abs_(double a)
+    {
+        return __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffll);
+    }
+    static __device__ __forceinline__ double half_(double a)
+    {
+        bool ok;
+        double r = f64i::scale2_rn(a, -1, ok);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (!ok) r = fp64_mul(0.5, a);
+        }
+        return r;
+    }
+    static __device__ __forceinline__ double twice(double a)
+    {
+        bool ok;
+        double r = f64i::scale2_rn(a, 1, ok);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (!ok) r = fp64_mul(2.0, a);
+        }
+        return r;
+    }
+};
+
+// ... and the products the flux marks as movable (mul2) on the integer pipes.
+struct ArIntMul : ArIntDivSqrt {
+    static __device__ __forceinline__ double mul2(double a, double b)
+    {
+        bool ok;
+        double r = f64i::mul_rn(a, b, ok);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (!ok) r = fp64_mul(a, b);
+        }
+        return r;
     }
 };
 
@@ -71,15 +124,6 @@ __device__ __forceinline__ RoeCell<double> load_cell(const int64_t* __restrict__
 {
     return roe_cell<double, A>(P.g, comp_value(q, n, i, 0, P), comp_value(q, n, i, 1, P),
                                comp_value(q, n, i, 2, P));
-}
-
-__device__ __forceinline__ RoeCell<double> shfl_cell(const RoeCell<double>& c, int src_delta, bool down)
-{
-    RoeCell<double> r;
-#define FQNM_SH(f) r.f = down ? __shfl_down_sync(0xffffffffu, c.f, src_delta) : __shfl_up_sync(0xffffffffu, c.f, src_delta)
-    FQNM_SH(rho); FQNM_SH(m); FQNM_SH(E); FQNM_SH(u); FQNM_SH(p); FQNM_SH(H); FQNM_SH(s);
-#undef FQNM_SH
-    return r;
 }
 
 // The Roe flux of one face and, for the integer components, its quantised
@@ -129,14 +173,21 @@ __global__ void k_euler_step(const int64_t* __restrict__ qin,
     const long long c = warp * EULER_OWN - 1 + lane;
     const long long j = c < 0 ? 0 : (c >= n ? n - 1 : c);
     const RoeCell<double> me = load_cell<A>(qin, n, j, P);
-    const RoeCell<double> right = shfl_cell(me, 1, true);   // lane 31: unused face
+    const RoeCell<double> right = roe_shfl<double>(me, 1, true);   // lane 31: unused face
     long long Fr[3], Fl[3];
     double Dr[3], Dl[3];
     transfer<A>(me, right, P, Fr, Dr, err);
+    // each component's left face: the integer transfer, or for a component
+    // kept in double its flux (a uniform branch on the mask)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
-        Dl[k] = __shfl_up_sync(0xffffffffu, Dr[k], 1);
+        if ((P.mask >> k) & 1) {
+            Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
+            Dl[k] = 0.0;
+        } else {
+            Fl[k] = 0;
+            Dl[k] = __shfl_up_sync(0xffffffffu, Dr[k], 1);
+        }
     }
     if (lane < 1 || lane > EULER_OWN || c >= n || !FQNM_IN_RANGE(c, n, err)) return;
 #pragma unroll
@@ -187,7 +238,9 @@ cudaError_t launch_euler_step(const int64_t* qin, int64_t* qout, int64_t n,
     const int block = 32;
     const long long warps = (n + EULER_OWN - 1) / EULER_OWN;
     const long long grid = (warps * 32 + block - 1) / block;
-    if (fp64_mode >= 2)
+    if (fp64_mode >= 3)
+        k_euler_step<ArIntMul><<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);
+    else if (fp64_mode == 2)
         k_euler_step<ArIntDivSqrt><<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);
     else
         k_euler_step<Ar<double>><<<(unsigned)grid, block, 0, st>>>(qin, qout, n, P, err, bflux);

@@ -43,7 +43,21 @@ __global__ void k_fp64_check(int op, int mode, const double* __restrict__ a,
         ri = __double_as_longlong(f64i::i64_scaled_to_f64(q, e));
         rf = __double_as_longlong(__dmul_rn((double)q, ldexp(1.0, e)));
         path = 1;
-    } else {                               // R(x * 2^e) as int64, e = (int)y
+    } else if (op == 5) {                  // x * y
+        bool ok;
+        const double r = f64i::mul_rn(x, y, ok);
+        ri = __double_as_longlong(ok ? r : __dmul_rn(x, y));
+        rf = __double_as_longlong(__dmul_rn(x, y));
+        path = ok;
+    } else if (op == 4) {                  // x * 2^k, k = (int)y in {-1, 1}
+        const int k = (int)y;
+        bool ok;
+        const double r = f64i::scale2_rn(x, k, ok);
+        const double f = __dmul_rn(x, k < 0 ? 0.5 : 2.0);
+        ri = __double_as_longlong(ok ? r : f);
+        rf = __double_as_longlong(f);
+        path = ok;
+    } else {                               // op 3: R(x * 2^e) as int64, e = (int)y
         const int e = (int)y;
         bool bad = false;
         ri = f64i::f64_scaled_round_to_i64(x, e, mode, bad);
@@ -66,7 +80,7 @@ extern "C" fqnm_status fqnm_fp64_check(int op, int rounding, const double* a, co
                                        size_t n, int64_t* out_int, int64_t* out_fp64,
                                        int32_t* out_path, void* stream)
 {
-    if (op < 0 || op > 3) return set_error(FQNM_ERR_ARG, "op must be 0..3");
+    if (op < 0 || op > 5) return set_error(FQNM_ERR_ARG, "op must be 0..5");
     if (rounding < 0 || rounding > 2) return set_error(FQNM_ERR_ARG, "rounding must be 0..2");
     if (n == 0) return FQNM_OK;
     if (!a || !b || !out_int || !out_fp64 || !out_path)

@@ -196,16 +196,6 @@ __device__ __forceinline__ RoeCell<T> fv_cell(const T* __restrict__ u, long long
     return roe_cell<T>(g, u[i], u[n + i], u[2 * n + i]);
 }
 
-template <typename T>
-__device__ __forceinline__ RoeCell<T> fv_shfl(const RoeCell<T>& c, bool down)
-{
-    RoeCell<T> r;
-#define FQNM_SH(f) r.f = down ? __shfl_down_sync(0xffffffffu, c.f, 1) : __shfl_up_sync(0xffffffffu, c.f, 1)
-    FQNM_SH(rho); FQNM_SH(m); FQNM_SH(E); FQNM_SH(u); FQNM_SH(p); FQNM_SH(H); FQNM_SH(s);
-#undef FQNM_SH
-    return r;
-}
-
 // Cell quantities formed once per cell and shared with the neighbouring
 // lanes, with the same warp layout as the integer Euler kernel: a warp loads
 // 32 cells (its 30 and one on each side, clamped: the transmissive ghost),
@@ -222,7 +212,7 @@ __global__ void k_euler_fv(T g, T lambda, const T* __restrict__ uin,
     const long long c = warp * EULER_FV_OWN - 1 + lane;
     const long long j = c < 0 ? 0 : (c >= n ? n - 1 : c);
     const RoeCell<T> me = fv_cell<T>(uin, n, j, g);
-    const RoeCell<T> right = fv_shfl<T>(me, true);
+    const RoeCell<T> right = roe_shfl<T>(me, 1, true);
     T Fr[3], Fl[3];
     roe_flux_cells<T>(g, me, right, Fr);
 #pragma unroll

@@ -3,6 +3,7 @@
 // Textbook Roe flux, no entropy fix, gamma-law gas, conserved U = (rho, m, E):
 //   iK = 1/rhoK, uK = mK*iK, pK = (g-1)*(EK - 0.5*(rhoK*(uK*uK))), HK = (EK+pK)*iK
 //   sL = sqrt(rhoL), sR = sqrt(rhoR), w = sL + sR, iw = 1/w
+//   (per cell, once: s, s*u, s*H and the physical flux components below)
 //   ut = (sL*uL + sR*uR)*iw, Ht = (sL*HL + sR*HR)*iw
 //   ct = sqrt((g-1)*(Ht - 0.5*(ut*ut)))
 //   jumps d0, d1, d2 of rho, m, E; wave strengths
@@ -21,28 +22,40 @@ namespace fqnm {
 
 template <typename T> struct Ar;
 
+// half_(x) = 0.5*x and twice(x) = 2*x are exact scalings by a power of two
+// (a policy may form them on the exponent field instead).
 template <> struct Ar<double> {
+    static __device__ __forceinline__ double half_(double a) { return __dmul_rn(0.5, a); }
+    static __device__ __forceinline__ double twice(double a) { return __dmul_rn(2.0, a); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    // mul2: a product that a policy may move off the FP64 unit (same result)
+    static __device__ __forceinline__ double mul2(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
     static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
     static __device__ __forceinline__ double abs_(double a) { return fabs(a); }
 };
 
 template <> struct Ar<float> {
+    static __device__ __forceinline__ float half_(float a) { return __fmul_rn(0.5f, a); }
+    static __device__ __forceinline__ float twice(float a) { return __fmul_rn(2.0f, a); }
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float mul2(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
     static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
     static __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
 };
 
-// The quantities of one cell that both of its faces use.
+// The quantities of one cell that both of its faces use: the conserved
+// state, s = sqrt(rho), the products s*u and s*H of the Roe averages, and
+// the physical flux's momentum and energy components f1 = m*u + p and
+// f2 = u*(E + p) (the same operations as in the flux, formed once per cell).
 template <typename T>
 struct RoeCell {
-    T rho, m, E, u, p, H, s;
+    T rho, m, E, s, su, sH, f1, f2;
 };
 
 // A: the arithmetic (Ar<T>, or a policy with the same members that forms
@@ -50,17 +63,35 @@ struct RoeCell {
 template <typename T, class A = Ar<T>>
 __device__ __forceinline__ RoeCell<T> roe_cell(T g, T rho, T m, T E)
 {
-    const T gm1 = A::sub(g, T(1)), half = T(0.5);
+    const T gm1 = A::sub(g, T(1));
     RoeCell<T> c;
     c.rho = rho;
     c.m = m;
     c.E = E;
     const T inv = A::div(T(1), rho);
-    c.u = A::mul(m, inv);
-    c.p = A::mul(gm1, A::sub(E, A::mul(half, A::mul(rho, A::mul(c.u, c.u)))));
-    c.H = A::mul(A::add(E, c.p), inv);
+    const T u = A::mul(m, inv);
+    const T p = A::mul(gm1, A::sub(E, A::half_(A::mul(rho, A::mul(u, u)))));
+    const T Ep = A::add(E, p);
+    const T H = A::mul(Ep, inv);
     c.s = A::sqrt_(rho);
+    c.su = A::mul(c.s, u);
+    c.sH = A::mul(c.s, H);
+    c.f1 = A::add(A::mul(m, u), p);
+    c.f2 = A::mul(u, Ep);
     return c;
+}
+
+// A cell's quantities from the lane `delta` above (down = true) or below.
+template <typename T>
+__device__ __forceinline__ RoeCell<T> roe_shfl(const RoeCell<T>& c, int delta, bool down)
+{
+    RoeCell<T> r;
+#define FQNM_SH(f) r.f = down ? __shfl_down_sync(0xffffffffu, c.f, delta) \
+                              : __shfl_up_sync(0xffffffffu, c.f, delta)
+    FQNM_SH(rho); FQNM_SH(m); FQNM_SH(E); FQNM_SH(s); FQNM_SH(su); FQNM_SH(sH);
+    FQNM_SH(f1); FQNM_SH(f2);
+#undef FQNM_SH
+    return r;
 }
 
 // The Roe flux between two cells whose quantities are already formed (the
@@ -68,33 +99,34 @@ __device__ __forceinline__ RoeCell<T> roe_cell(T g, T rho, T m, T E)
 template <typename T, class A = Ar<T>>
 __device__ __forceinline__ void roe_flux_cells(T g, const RoeCell<T>& L, const RoeCell<T>& R, T* F)
 {
-    const T one = T(1), half = T(0.5), gm1 = A::sub(g, one);
-    const T rhoL = L.rho, mL = L.m, EL = L.E, uL = L.u, pL = L.p, HL = L.H, sL = L.s;
-    const T rhoR = R.rho, mR = R.m, ER = R.E, uR = R.u, pR = R.p, HR = R.H, sR = R.s;
-    const T w = A::add(sL, sR), iw = A::div(one, w);
-    const T ut = A::mul(A::add(A::mul(sL, uL), A::mul(sR, uR)), iw);
-    const T Ht = A::mul(A::add(A::mul(sL, HL), A::mul(sR, HR)), iw);
+    const T one = T(1), gm1 = A::sub(g, one);
+    const T w = A::add(L.s, R.s), iw = A::div(one, w);
+    const T ut = A::mul(A::add(L.su, R.su), iw);
+    const T Ht = A::mul(A::add(L.sH, R.sH), iw);
     const T uu = A::mul(ut, ut);
-    const T ct = A::sqrt_(A::mul(gm1, A::sub(Ht, A::mul(half, uu))));
-    const T d0 = A::sub(rhoR, rhoL), d1 = A::sub(mR, mL), d2 = A::sub(ER, EL);
+    const T huu = A::half_(uu);
+    const T ct = A::sqrt_(A::mul(gm1, A::sub(Ht, huu)));
+    const T d0 = A::sub(R.rho, L.rho), d1 = A::sub(R.m, L.m), d2 = A::sub(R.E, L.E);
     const T a2 = A::mul(A::div(gm1, A::mul(ct, ct)),
                         A::sub(A::add(A::mul(d0, A::sub(Ht, uu)), A::mul(ut, d1)), d2));
     const T a1 = A::div(A::sub(A::sub(A::mul(d0, A::add(ut, ct)), d1), A::mul(ct, a2)),
-                        A::mul(T(2), ct));
+                        A::twice(ct));
     const T a3 = A::sub(d0, A::add(a1, a2));
     const T l1 = A::abs_(A::sub(ut, ct)), l2 = A::abs_(ut), l3 = A::abs_(A::add(ut, ct));
     const T uct = A::mul(ut, ct);
     const T r1[3] = {one, A::sub(ut, ct), A::sub(Ht, uct)};
-    const T r2[3] = {one, ut, A::mul(half, uu)};
+    const T r2[3] = {one, ut, huu};
     const T r3[3] = {one, A::add(ut, ct), A::add(Ht, uct)};
-    const T fL[3] = {mL, A::add(A::mul(mL, uL), pL), A::mul(uL, A::add(EL, pL))};
-    const T fR[3] = {mR, A::add(A::mul(mR, uR), pR), A::mul(uR, A::add(ER, pR))};
+    const T fL[3] = {L.m, L.f1, L.f2};
+    const T fR[3] = {R.m, R.f1, R.f2};
     const T la1 = A::mul(l1, a1), la2 = A::mul(l2, a2), la3 = A::mul(l3, a3);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const T diss = A::add(A::add(A::mul(la1, r1[k]), A::mul(la2, r2[k])),
-                              A::mul(la3, r3[k]));
-        F[k] = A::sub(A::mul(half, A::add(fL[k], fR[k])), A::mul(half, diss));
+        // the eigenvectors' first components are 1: x*1 = x exactly
+        const T diss = k == 0 ? A::add(A::add(la1, la2), la3)
+                              : A::add(A::add(A::mul2(la1, r1[k]), A::mul2(la2, r2[k])),
+                                       A::mul2(la3, r3[k]));
+        F[k] = A::sub(A::half_(A::add(fL[k], fR[k])), A::half_(diss));
     }
 }
 

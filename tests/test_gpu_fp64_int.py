@@ -128,7 +128,37 @@ def test_scaled_rounding_matches_fp64(rounding):
     assert np.array_equal((path >> 1) & 1, (path >> 2) & 1)   # out of range alike
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_multiplication_matches_fp64():
+    rng = np.random.default_rng(106)
+    n = 1 << 22
+    a = doubles(rng, n)
+    b = doubles(rng, n)
+    near_a = doubles(rng, n, 800, 1250)
+    near_b = doubles(rng, n, 800, 1250)
+    # products with few significant bits (exact) and at rounding ties:
+    # (2^26 + odd)^2 has its discarded half exactly at the rounding bit
+    x = (rng.integers(1 << 26, 1 << 27, 1 << 16) | 1).astype(np.float64)
+    s = specials()
+    sa, sb = np.meshgrid(s, s)
+    A = np.concatenate([a, near_a, x, x * 3.0, sa.ravel(), np.zeros(64)])
+    B = np.concatenate([b, near_b, x, x, sb.ravel(), doubles(rng, 64)])
+    gi, gf, path = run(5, A, B)
+    assert_same(gi, gf, A, B)
+    assert (path[n: 2 * n] & 1).all()
+
+
+def test_halving_and_doubling_match_fp64():
+    rng = np.random.default_rng(105)
+    n = 1 << 20
+    x = np.concatenate([doubles(rng, n), doubles(rng, 4096, 1, 3), doubles(rng, 4096, 2044, 2046),
+                        specials()])
+    for k in (-1.0, 1.0):
+        gi, gf, path = run(4, x, np.full(x.size, k))
+        assert_same(gi, gf, x)
+        assert (path[:n] & 1).mean() > 0.99
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("mask", [7, 1])
 def test_roe_step_every_fp64_mode_matches_oracle(orc, mode, mask):
     """A Sod tube (and the density-only variant) for 300 steps in each FP64
