@@ -246,7 +246,8 @@ def run_gpu(args):
     # stepping region; average launch duration from the events around it
     avg_launch_s = (sum(region_ms) / 1e3) / max(step_launches, 1)
     updates_per_launch = n * (T * args.steps) / max(step_launches, 1)
-    kernel_tag = "k_step_tb:L%d:V%d" % (stats["layout"], stats["cells_per_thread"])
+    kernel_tag = "k_step_tb:L%d:V%d:B%d" % (stats["layout"], stats["cells_per_thread"],
+                                            stats["block"])
     counters = profiled_counters(kernel_tag, B.kernel_digest(),
                                  "burgers_lf_2^20_cells_K%d" % stats["k"])
     roofline = stepping_roofline(counters, updates_per_launch, avg_launch_s, clk, kernel_tag)
@@ -332,6 +333,7 @@ def run_gpu(args):
             result["serving"] = serving
         if workloads:
             result["workloads"] = workloads
+        result["summary"] = summary(result)          # last, so a log's tail shows it
         print(json.dumps(result))
     s.close()
     if world > 1:
@@ -339,6 +341,38 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def summary(r: dict) -> dict:
+    """The headline figures of every workload in one short object."""
+    w = r.get("workloads") or {}
+    out = {"burgers_1m": r.get("value"), "e2e": (r.get("e2e") or {}).get("value"),
+           "issue_frac": (r.get("roofline") or {}).get("frac")}
+    if "high_frequency_16m" in w:
+        out["high_frequency_16m"] = w["high_frequency_16m"]["value"]
+    for k in ("sod_65k", "sod_1m"):
+        if k in w:
+            out[k] = {x: w[k].get(x) for x in ("seconds", "face_evaluations_per_s",
+                                               "integer_speedup_vs_fv64", "l1_density_vs_exact",
+                                               "totals_balance_exact")}
+    for k in ("burgers_2d_8192", "burgers_3d_512"):
+        if k in w:
+            out[k] = w[k]["default"]["value"]
+    sv = r.get("serving")
+    if sv:
+        out["serving"] = {"online": sv["batched_online"]["value"],
+                          "p50_ms": sv["batched_online"]["p50_ms"],
+                          "p99_ms": sv["batched_online"]["p99_ms"],
+                          "offline": sv["batched_offline"]["value"],
+                          "identical": sv["results_identical"]}
+    fv = r.get("fv_baseline")
+    if fv:
+        out["fv32"] = fv["fp32"]["value"]
+        out["fv64"] = fv["fp64"]["value"]
+    par = r.get("parity")
+    if par:
+        out["parity_all_equal"] = par.get("all_equal")
+    return out
 
 
 def issue_peak(clk: dict):
@@ -500,7 +534,7 @@ def other_workloads(F, torch, stream, clk=None, finals=None):
         if name == "high_frequency_16m" and st["kernel"] == 2 and launches:
             # the large line: its own roofline object (the state, 2 x 64 MiB,
             # is about the L2's size, so HBM could bind here)
-            tag = "k_step_tb:L%d:V%d" % (st["layout"], st["cells_per_thread"])
+            tag = "k_step_tb:L%d:V%d:B%d" % (st["layout"], st["cells_per_thread"], st["block"])
             c = profiled_counters(tag, B.kernel_digest(),
                                   "upwind_closed_2^24_cells_K%d" % st["k"])
             out[name]["roofline"] = stepping_roofline(c, p.n * p.steps / launches,
@@ -545,8 +579,23 @@ def other_workloads(F, torch, stream, clk=None, finals=None):
         "l1_density_integer_vs_fv64": float(p.dx * np.abs(u[0] - ufv[0]).sum()),
         "totals_balance_exact": all(inv["mass"][k] == q0[k] - inv["boundary_flux"][k]
                                     for k in range(3)),
-        "bound": "fp64 pipe (Roe flux, about 100 FP64 operations per face)",
+        "bound": "FP64 unit (about 72 FP64 additions and multiplications per face; the "
+                 "divisions, square roots, conversions and rounding run on the integer "
+                 "pipes, FQNM_OPT_FP64 = 2)",
     }
+    # the same run with every IEEE double step on the FP64 unit (FQNM_OPT_FP64 = 0)
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive", fp64=0)
+    F.fqnm_set_stream(s.h, stream)
+    with torch.cuda.stream(stream):
+        s.load_field(U0, p.n, on_device=True)
+        t_fp64 = _timed(stream, torch, lambda: (F.fqnm_load_field(s.h, U0, p.n, on_device=True),
+                                                F.fqnm_step(s.h, p.steps)), 1)
+    same = bool(np.array_equal(s.observe(), u))
+    s.close()
+    out["sod_65k"]["fp64_unit_only_seconds"] = t_fp64
+    out["sod_65k"]["fp64_unit_only_identical"] = same
+    out["sod_1m"] = sod_large(F, torch, stream, finals)
     # Sod with the density channel alone quantised (§3.3's prototype)
     s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
                  "transmissive", quantise_mask=1)
@@ -572,6 +621,50 @@ def other_workloads(F, torch, stream, clk=None, finals=None):
     out["burgers_sine_convergence"] = convergence_sweep(F, torch, stream)
     out["level_statistics_1m"] = level_statistics(F, torch, stream)
     return out
+
+
+def sod_large(F, torch, stream, finals, n=1 << 20, window=20_000):
+    """Sod on 2^20 cells: the integer Roe step against the FP64 Roe FV
+    baseline over the first 20,000 steps (device-timed), and the whole run
+    to t = 0.2 (919,210 steps, device-timed, once) with the exact balance of
+    all three totals; the L1 density error against the exact Riemann solution
+    and the full-state parity of the first 2000 steps are added by the CPU
+    leg."""
+    p = I.sod_problem(n=n)
+    U0 = torch.from_numpy(p.U0.reshape(-1).copy()).cuda()
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive")
+    F.fqnm_set_stream(s.h, stream)
+    with torch.cuda.stream(stream):
+        s.load_field(U0, p.n, on_device=True)
+        t_int = _timed(stream, torch, lambda: (F.fqnm_load_field(s.h, U0, p.n, on_device=True),
+                                               F.fqnm_step(s.h, window)), 1)
+        if finals is not None:
+            F.fqnm_load_field(s.h, U0, p.n, on_device=True)
+            F.fqnm_step(s.h, 2000)
+            finals["sod_1m_2000"] = (p, s.state().reshape(3, -1))
+        t_full = _timed(stream, torch, lambda: (F.fqnm_load_field(s.h, U0, p.n, on_device=True),
+                                                F.fqnm_step(s.h, p.steps)), 1)
+    inv = F.fqnm_invariants(s.h)
+    u = s.observe()
+    s.close()
+    fv = F.fqnm_fv_create(F.make_flux("euler_roe", gamma=p.gamma), p.dx, p.dt, "transmissive", 64)
+    F.fqnm_fv_set_stream(fv, stream)
+    with torch.cuda.stream(stream):
+        F.fqnm_fv_load_device(fv, U0, p.n)
+        t_fv = _timed(stream, torch, lambda: (F.fqnm_fv_load_device(fv, U0, p.n),
+                                              F.fqnm_fv_step(fv, window)), 1)
+    F.fqnm_fv_destroy(fv)
+    q0 = [int(round(v)) for v in (p.U0.sum(axis=1) / np.array(p.delta))]
+    if finals is not None:
+        finals["sod_1m_rho"] = (p, u[0].copy())
+    return {"n_cells": p.n, "time_steps": p.steps, "t_end": 0.2,
+            "seconds": t_full, "face_evaluations_per_s": (p.n + 1) * p.steps / t_full,
+            "first_steps": window, "first_steps_seconds": t_int,
+            "fv64_roe_first_steps_seconds": t_fv, "integer_speedup_vs_fv64": t_fv / t_int,
+            "totals_balance_exact": all(inv["mass"][k] == q0[k] - inv["boundary_flux"][k]
+                                        for k in range(3)),
+            "l1_density_vs_exact": None}
 
 
 def nd_workload(F, torch, stream, dims, steps):
@@ -794,6 +887,17 @@ def oracle_parity(p, final_q, sample, finals) -> dict:
                                      "cells_differing": diff, "equal": diff == 0,
                                      "oracle": "full state (rho, m, E) from dependency "
                                                "windows"}
+    if "sod_1m_2000" in finals:
+        ps, q2000 = finals["sod_1m_2000"]
+        t0 = time.perf_counter()
+        q0s = np.stack([O.quantise(ps.U0[k], ps.delta[k]) for k in range(3)]).astype(np.int64)
+        want = O.euler_step_by_windows(q0s, 2000, ps.gamma, ps.delta, ps.dx, ps.dt)
+        diff = int((q2000 != want).any(axis=0).sum())
+        out["sod_1m_2000_steps"] = {"cells": int(ps.n), "time_steps": 2000,
+                                    "cells_differing": diff, "equal": diff == 0,
+                                    "oracle": "full state (rho, m, E) from dependency windows, "
+                                              "%d host processes, %.1f s"
+                                              % (os.cpu_count() or 1, time.perf_counter() - t0)}
     out["all_equal"] = all(v.get("equal", False) for v in out.values() if isinstance(v, dict))
     return out
 
@@ -811,6 +915,11 @@ def sod_accuracy(finals, workloads):
     if "sod_65k_fv64" in finals:
         workloads["sod_65k"]["l1_density_fv64_vs_exact"] = float(
             p.dx * np.abs(finals["sod_65k_fv64"] - rex).sum())
+    if "sod_1m_rho" in finals and "sod_1m" in workloads:
+        p, rho = finals["sod_1m_rho"]
+        x = I.cell_centres(p.n)
+        rex, _, _ = O.riemann_sample(p.gamma, I.SOD_LEFT, I.SOD_RIGHT, 0.5, I.SOD_T_END, x)
+        workloads["sod_1m"]["l1_density_vs_exact"] = float(p.dx * np.abs(rho - rex).sum())
 
 
 def _oracle_request(job):

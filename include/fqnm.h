@@ -152,7 +152,10 @@ typedef enum {
                                 of a call in one launch.  Auto takes 4 for periodic lines of
                                 at most 512 cells when no temporal-blocked plan option is set,
                                 else 2 (periodic) or 1. */
-    FQNM_OPT_LAYOUT = 1,     /* 0 auto, 1 interleaved, 2 blocked (cells per thread contiguous) */
+    FQNM_OPT_LAYOUT = 1,     /* 0 auto, 1 interleaved, 2 blocked (cells per thread contiguous),
+                                3 / 4 runs of 4 / 8 consecutive cells per lane (a warp-wide
+                                table gather then covers 128 / 256 neighbouring cells; needs
+                                at least two runs per lane) */
     FQNM_OPT_CELLS_PER_THREAD = 2, /* 4, 8, 16 or 32; 0 auto */
     FQNM_OPT_BLOCK = 3,      /* threads per block, multiple of 32, <= 512 (32: one warp, no barrier); 0 auto */
     FQNM_OPT_K = 4,          /* time steps per launch (temporal block depth); 0 auto */

@@ -34,7 +34,7 @@ enum : unsigned {
     ERRBIT_BOUNDS = 8u,     // (checked builds) a computed index left its buffer
 };
 
-enum Layout : int { LAYOUT_INTERLEAVED = 1, LAYOUT_BLOCKED = 2 };
+enum Layout : int { LAYOUT_INTERLEAVED = 1, LAYOUT_BLOCKED = 2, LAYOUT_RUNS4 = 3, LAYOUT_RUNS8 = 4 };
 enum Evaluator : int { EVAL_TABLE = 1, EVAL_CLOSED_FORM = 2 };
 
 // Integer closed form phi(q) = R(q * num / den) for den > 0, num > 0,

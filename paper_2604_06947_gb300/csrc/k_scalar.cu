@@ -198,11 +198,20 @@ cudaError_t dispatch_tb(const Ev& ev, const Plan& p, const int* qin, int* qout,
             return launch_tb_t<Ev, VV, LAYOUT_INTERLEAVED>(ev, p.block, p.pdl, qin, qout, n, k, err, st); \
         return launch_tb_t<Ev, VV, LAYOUT_BLOCKED>(ev, p.block, p.pdl, qin, qout, n, k, err, st); \
     }
+#define FQNM_TB_RUNS(VV, LL)                                                      \
+    if (p.v == VV && p.layout == LL)                                              \
+        return launch_tb_t<Ev, VV, LL>(ev, p.block, p.pdl, qin, qout, n, k, err, st);
+    FQNM_TB_RUNS(8, LAYOUT_RUNS4)
+    FQNM_TB_RUNS(16, LAYOUT_RUNS4)
+    FQNM_TB_RUNS(32, LAYOUT_RUNS4)
+    FQNM_TB_RUNS(16, LAYOUT_RUNS8)
+    FQNM_TB_RUNS(32, LAYOUT_RUNS8)
     FQNM_TB_CASE(4)
     FQNM_TB_CASE(8)
     FQNM_TB_CASE(16)
     FQNM_TB_CASE(32)
 #undef FQNM_TB_CASE
+#undef FQNM_TB_RUNS
     return cudaErrorInvalidValue;
 }
 
@@ -213,7 +222,10 @@ bool tb_plan_supported(const RuleView& r, const Plan& p)
     (void)r;
     if (p.v != 4 && p.v != 8 && p.v != 16 && p.v != 32) return false;
     if (p.block < 32 || p.block > TB_MAX_BLOCK || p.block % 32) return false;
-    if (p.layout != LAYOUT_INTERLEAVED && p.layout != LAYOUT_BLOCKED) return false;
+    if (p.layout < LAYOUT_INTERLEAVED || p.layout > LAYOUT_RUNS8) return false;
+    // a runs layout needs at least two runs per lane (one run is BLOCKED)
+    if (p.layout == LAYOUT_RUNS4 && p.v < 8) return false;
+    if (p.layout == LAYOUT_RUNS8 && p.v < 16) return false;
     return p.k >= 1 && 2LL * p.k < (long long)p.block * p.v;
 }
 

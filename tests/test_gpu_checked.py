@@ -25,7 +25,9 @@ q0 = orc.quantise(p.u0, p.delta)
 want = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 130, alpha=p.alpha)
 for plan in (dict(layout=1, cells_per_thread=4, block=32, k=8),
              dict(layout=2, cells_per_thread=8, block=128, k=64),
-             dict(layout=2, cells_per_thread=32, block=512, k=128), dict(kernel=1)):
+             dict(layout=2, cells_per_thread=32, block=512, k=128),
+             dict(layout=3, cells_per_thread=16, block=32, k=7),
+             dict(layout=4, cells_per_thread=16, block=64, k=64), dict(kernel=1)):
     s = F.Solver.for_problem(p, graph=0, **plan).load(q0)
     s.step(130)
     assert np.array_equal(s.state(), want), plan

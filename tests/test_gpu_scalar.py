@@ -142,7 +142,11 @@ PLANS = [dict(kernel=1), dict(kernel=4)] + [
      dict(kernel=2, layout=2, cells_per_thread=16, block=512, k=64)] + [
     dict(kernel=2, layout=L, cells_per_thread=v, block=32, k=k)     # one warp per block
     for L in (1, 2) for v in (4, 8, 16) for k in (1, 7, 32)
-]
+] + [
+    dict(kernel=2, layout=L, cells_per_thread=v, block=b, k=k)      # runs of 4 or 8 cells
+    for L, v in ((3, 8), (3, 16), (3, 32), (4, 16), (4, 32)) for b in (32, 64) for k in (1, 7, 32)
+] + [dict(kernel=2, layout=3, cells_per_thread=16, block=256, k=64),
+     dict(kernel=2, layout=2, cells_per_thread=32, block=32, k=64)]
 
 
 @pytest.mark.parametrize("plan", PLANS, ids=lambda d: "-".join("%s%s" % kv for kv in d.items()))

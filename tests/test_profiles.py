@@ -7,6 +7,8 @@ from paper_2604_06947_gb300 import build as B
 
 
 def test_traffic_counters_match_the_current_kernel():
-    c = bench.profiled_counters("k_step_tb:L2:V8", B.kernel_digest())
-    assert c.get("dram_bytes_per_launch", 0) > 0, "recapture profiles/traffic.txt"
-    assert c.get("warp_instructions_per_launch", 0) > 0
+    for tag, workload in (("k_step_tb:L4:V16:B64", "burgers_lf_2^20_cells_K64"),
+                          ("k_step_tb:L2:V8:B128", "upwind_closed_2^24_cells_K64")):
+        c = bench.profiled_counters(tag, B.kernel_digest(), workload)
+        assert c.get("dram_bytes_per_launch", 0) > 0, "recapture profiles/traffic.txt"
+        assert c.get("warp_instructions_per_launch", 0) > 0
