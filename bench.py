@@ -999,6 +999,59 @@ def run_reference(args):
     return res
 
 
+def run_sod_full(args):
+    """Sod on 2^m cells to t = 0.2 on one GPU, device-timed as one run with
+    the SM clocks sampled: the integer Roe step's full run, the exact balance
+    of all three totals against the counted boundary transfer, the L1
+    density error against the exact Riemann solution, and (CPU leg) the
+    whole state after the first 2000 steps against the oracle."""
+    import torch
+    from paper_2604_06947_gb300 import fqnm as F
+    torch.cuda.set_device(0)
+    F.load()
+    p = I.sod_problem(n=1 << args.sod_full)
+    stream = torch.cuda.Stream()
+    U0 = torch.from_numpy(p.U0.reshape(-1).copy()).cuda()
+    s = F.Solver(F.make_flux("euler_roe", gamma=p.gamma), list(p.delta), p.dx, p.dt,
+                 "transmissive")
+    F.fqnm_set_stream(s.h, stream)
+    with torch.cuda.stream(stream):
+        s.load_field(U0, p.n, on_device=True)
+        F.fqnm_step(s.h, 2000)
+        q2000 = s.state().reshape(3, -1)
+        F.fqnm_load_field(s.h, U0, p.n, on_device=True)
+        stream.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        F.fqnm_step(s.h, p.steps)
+        b.record(stream)
+        b.synchronize()
+        clk = clocks.stop()
+    secs = a.elapsed_time(b) / 1e3
+    inv = F.fqnm_invariants(s.h)
+    u = s.observe()
+    s.close()
+    q0 = [int(round(v)) for v in (p.U0.sum(axis=1) / np.array(p.delta))]
+    res = {"workload": "sod_%d_cells_to_t0.2" % p.n, "n_cells": p.n, "time_steps": p.steps,
+           "seconds": secs, "face_evaluations_per_s": (p.n + 1) * p.steps / secs,
+           "totals_balance_exact": all(inv["mass"][k] == q0[k] - inv["boundary_flux"][k]
+                                       for k in range(3)),
+           "boundary_transfer": inv["boundary_flux"], "clocks": clk}
+    if not args.no_cpu:
+        from oracle import oracle as O
+        x = I.cell_centres(p.n)
+        rex, _, _ = O.riemann_sample(p.gamma, I.SOD_LEFT, I.SOD_RIGHT, 0.5, I.SOD_T_END, x)
+        res["l1_density_vs_exact"] = float(p.dx * np.abs(u[0] - rex).sum())
+        qs = np.stack([O.quantise(p.U0[k], p.delta[k]) for k in range(3)]).astype(np.int64)
+        want = O.euler_step_by_windows(qs, 2000, p.gamma, p.delta, p.dx, p.dt)
+        diff = int((q2000 != want).any(axis=0).sum())
+        res["parity_first_2000_steps"] = {"cells_differing": diff, "equal": diff == 0}
+    print(json.dumps(res))
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1010,9 +1063,13 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the batched serving stream")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the other workloads (high-frequency 16M, linear 1k, Sod)")
+    ap.add_argument("--sod-full", type=int, default=0, metavar="M",
+                    help="only run Sod on 2^M cells to t = 0.2 and print its record")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
+    if args.sod_full:
+        run_sod_full(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
