@@ -285,8 +285,10 @@ fqnm_status fqnm_invariants(fqnm_solver* s, const fqnm_solver* other,
  * out[2] = sum |q - other| (0 when other is NULL).  q and other are device
  * pointers to n int32 (caller-owned, only read); out is a host int64[3].  Runs
  * on `stream` (NULL: legacy default stream) and waits for it before returning.
- * Its scratch is one static device array reserved on each GPU that loads the
- * library until the process exits; it calls no cudaMalloc or cudaFree.
+ * Its scratch is one static device array (about 98 KB) reserved on each GPU
+ * where the library's device code is loaded (with CUDA's lazy module loading,
+ * at the first call on that device) until the process exits; it calls no
+ * cudaMalloc or cudaFree.
  *   - n must be 1 .. FQNM_NOALLOC_MAX_CELLS, else FQNM_ERR_ARG (no launch).
  *   - The first call on each device looks up the array's address with that
  *     device current; make it before any stream capture on that device.
@@ -513,15 +515,24 @@ fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
 fqnm_status fqnm_batch_destroy(fqnm_batch* b);
 /* Execution plan of the batched launch (0 keeps a value): cells per thread
  * (4, 8, 16), threads per block, steps per epoch K, layout (1 interleaved, 2
- * blocked).  Takes effect at the next epoch; results do not depend on it. */
+ * blocked, 3 runs of 4 cells with 8 or 16 cells per thread, 4 runs of 8 with
+ * 16).  Takes effect at the next epoch (epochs already enqueued finish
+ * first); results do not depend on it. */
 fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
                                 int k, int layout);
 /* Autotune the plan online: the next epochs with work try each candidate
- * (cells per thread 8/16, 32/128/256 threads, K 32/64/128, halo work at most
- * half the tile) for epochs_per_plan epochs, then keep the one with the
- * least epoch wall time per cell update (the host's admission, graph replay
- * and synchronisation included, a fixed cost per epoch). */
+ * (blocked or runs of 8 cells, cells per thread 8/16, 32/128/256 threads, K
+ * 32/64/128, halo work at most half the tile) for epochs_per_plan epochs,
+ * then keep the one with the least wall time between epoch retirements per
+ * cell update (the host's admission and bookkeeping overlap the GPU's
+ * epochs, so this is the period the stream sees). */
 fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan);
+/* The quanta added on each side of a request's state range when its
+ * transfer maps are built (default 1024), for requests submitted after this
+ * call.  A state that leaves the maps restarts its problem with the margin
+ * widened (x4, at least 4096); the result is the same.  FQNM_ERR_ARG for a
+ * negative margin. */
+fqnm_status fqnm_batch_set_margin(fqnm_batch* b, int64_t margin);
 /* The current plan; *tuning = 1 while candidates are still being tried. */
 fqnm_status fqnm_batch_get_plan(fqnm_batch* b, int* cells_per_thread, int* block,
                                 int* k, int* layout, int* tuning);

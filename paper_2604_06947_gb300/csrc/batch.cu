@@ -14,6 +14,11 @@
 //      kernel, advancing that problem by min(K, remaining) steps;
 //   3. copies finished states to host memory, frees their memory and slots,
 //      and records submit-to-result latency.
+// Epochs are pipelined: epoch e is enqueued before the host waits for epoch
+// e-1 and reads its retirements (finished states, error words, rule
+// checks), so the GPU runs e while the host retires e-1 and admits for e+1.
+// A problem's memory is released only once no enqueued epoch uses it; an
+// error seen one epoch late restarts the problem after that epoch too.
 // States stay resident on the device between epochs.  Problems are
 // independent and the arithmetic is integer, so each result is bit-identical
 // to solving the problem alone.  A range escape (error bit of that problem)
@@ -96,11 +101,20 @@ using BatchKernel = void (*)(const BatchDesc*, const long long*, const BatchHead
 BatchKernel batch_kernel(int v, int layout, int block)
 {
     const bool w = block == 32;
+    if (layout == LAYOUT_RUNS8) {
+        if (v == 16) return w ? k_batch_step<16, LAYOUT_RUNS8, true> : k_batch_step<16, LAYOUT_RUNS8, false>;
+        return nullptr;
+    }
+    if (layout == LAYOUT_RUNS4) {
+        if (v == 8) return w ? k_batch_step<8, LAYOUT_RUNS4, true> : k_batch_step<8, LAYOUT_RUNS4, false>;
+        if (v == 16) return w ? k_batch_step<16, LAYOUT_RUNS4, true> : k_batch_step<16, LAYOUT_RUNS4, false>;
+        return nullptr;
+    }
     if (layout == LAYOUT_BLOCKED) {
         if (v == 4) return w ? k_batch_step<4, LAYOUT_BLOCKED, true> : k_batch_step<4, LAYOUT_BLOCKED, false>;
         if (v == 8) return w ? k_batch_step<8, LAYOUT_BLOCKED, true> : k_batch_step<8, LAYOUT_BLOCKED, false>;
         if (v == 16) return w ? k_batch_step<16, LAYOUT_BLOCKED, true> : k_batch_step<16, LAYOUT_BLOCKED, false>;
-    } else {
+    } else if (layout == LAYOUT_INTERLEAVED) {
         if (v == 4) return w ? k_batch_step<4, LAYOUT_INTERLEAVED, true> : k_batch_step<4, LAYOUT_INTERLEAVED, false>;
         if (v == 8) return w ? k_batch_step<8, LAYOUT_INTERLEAVED, true> : k_batch_step<8, LAYOUT_INTERLEAVED, false>;
         if (v == 16) return w ? k_batch_step<16, LAYOUT_INTERLEAVED, true> : k_batch_step<16, LAYOUT_INTERLEAVED, false>;
@@ -165,6 +179,19 @@ struct Slot {
     bool cf_candidate = false;
     int k_this_epoch = 0;
     size_t out_off = 0;              // where its final state lands in the staging area
+    long long first_epoch = -1;      // the first enqueued epoch that steps it
+    long long last_epoch = -1;       // the last enqueued epoch that steps it
+    long long check_epoch = -1;      // the epoch whose read-back carries its rule check
+    long long finish_epoch = -1;     // the epoch that copies its final state out
+    bool restarting = false;         // an error was seen: restart once no epoch uses it
+};
+
+struct Inflight {                    // an enqueued epoch not yet retired
+    long long epoch = 0;
+    int np = 0;                      // problems it steps
+    uint64_t updates = 0;            // cell updates it performs
+    uint64_t t0 = 0;                 // host clock when it was enqueued
+    int cand = -1;                   // autotuning candidate it runs, or -1
 };
 
 }  // namespace
@@ -188,21 +215,31 @@ struct fqnm_batch {
     unsigned* d_err = nullptr;
     unsigned long long* d_check = nullptr;
     long long* d_range = nullptr;             // [2*slot]: min, max of a device submission
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t side = nullptr;              // device submissions' state ranges
     double gpu_ms = 0.0;
-    // pinned
-    BatchDesc* h_desc = nullptr;
-    long long* h_prefix = nullptr;
-    BatchHeader* h_hdr = nullptr;
-    unsigned* h_err = nullptr;
-    unsigned long long* h_check = nullptr;
+    // per epoch parity (two epochs in flight): pinned descriptor tables and
+    // read-backs, the graph that uploads the tables and launches the kernel,
+    // and the events around it; the staging area is split in two halves
+    BatchDesc* h_desc[2] = {nullptr, nullptr};
+    long long* h_prefix[2] = {nullptr, nullptr};
+    BatchHeader* h_hdr[2] = {nullptr, nullptr};
+    unsigned* h_err[2] = {nullptr, nullptr};
+    unsigned long long* h_check[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    Plan graph_plan[2];
+    // ev0 / ev1 bracket the batched launch (GPU time); ev2 follows the
+    // epoch's copies and read-backs (its retirement waits on it)
+    cudaEvent_t ev0[2] = {nullptr, nullptr}, ev1[2] = {nullptr, nullptr}, ev2[2] = {nullptr, nullptr};
     long long* h_range = nullptr;
     int32_t* h_stage = nullptr;
-    size_t stage_ints = 0;
-    // plan and graph
+    size_t stage_ints = 0;                    // per half
+    // pipeline
+    long long next_epoch = 0;
+    std::deque<Inflight> inflight;
+    uint64_t last_retire_ns = 0;
+    // plan
     Plan plan;
     int grid = 0;
-    cudaGraphExec_t gexec = nullptr;
     // online autotuning: candidate plans tried on the first epochs with work,
     // scored by the epochs' wall time (host admission, replay and sync
     // included: a fixed cost per epoch that small K pays more often) per
@@ -211,15 +248,27 @@ struct fqnm_batch {
     std::vector<Plan> cands;
     std::vector<double> cand_ns;             // wall ns of the epochs, summed
     std::vector<uint64_t> cand_updates;
-    int tune_epoch = 0, tune_per_plan = 3;
+    std::vector<int> cand_retired;
+    int tune_launch = 0, tune_per_plan = 3;
     // counters
     uint64_t launches = 0, cell_updates = 0, epochs = 0;
     bool pack16 = false;                     // packed int16 tables (off: faster on GB300)
+    int64_t margin = 1024;                   // initial map margin of new requests
 };
 
 static void batch_free_device(fqnm_batch* b)
 {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (int pe = 0; pe < 2; ++pe) {
+        if (b->gexec[pe]) cudaGraphExecDestroy(b->gexec[pe]);
+        if (b->ev0[pe]) cudaEventDestroy(b->ev0[pe]);
+        if (b->ev1[pe]) cudaEventDestroy(b->ev1[pe]);
+        if (b->ev2[pe]) cudaEventDestroy(b->ev2[pe]);
+        cudaFreeHost(b->h_desc[pe]);
+        cudaFreeHost(b->h_prefix[pe]);
+        cudaFreeHost(b->h_hdr[pe]);
+        cudaFreeHost(b->h_err[pe]);
+        cudaFreeHost(b->h_check[pe]);
+    }
     cudaFree(b->arena);
     cudaFree(b->d_desc);
     cudaFree(b->d_prefix);
@@ -228,14 +277,8 @@ static void batch_free_device(fqnm_batch* b)
     cudaFree(b->d_check);
     cudaFree(b->d_range);
     cudaFreeHost(b->h_range);
-    if (b->ev0) cudaEventDestroy(b->ev0);
-    if (b->ev1) cudaEventDestroy(b->ev1);
-    cudaFreeHost(b->h_desc);
-    cudaFreeHost(b->h_prefix);
-    cudaFreeHost(b->h_hdr);
-    cudaFreeHost(b->h_err);
-    cudaFreeHost(b->h_check);
     cudaFreeHost(b->h_stage);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -294,26 +337,31 @@ extern "C" fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
     b->plan.v = 8;
     b->plan.block = 128;
     b->plan.k = 32;
-    b->stage_ints = (size_t)64 << 20;                 // 256 MiB pinned staging
+    b->stage_ints = (size_t)32 << 20;                 // 2 x 128 MiB pinned staging
     cudaError_t e = cudaSuccess;
     if (stream) b->stream = (cudaStream_t)stream;
     else { e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking); b->own_stream = true; }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->arena, b->budget);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, max_slots * sizeof(BatchDesc));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_prefix, (max_slots + 1) * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_hdr, sizeof(BatchHeader));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, max_slots * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_check, 4 * max_slots * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_desc, max_slots * sizeof(BatchDesc));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_prefix, (max_slots + 1) * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hdr, sizeof(BatchHeader));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_err, max_slots * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_check, 4 * max_slots * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_stage, b->stage_ints * sizeof(int32_t));
+    for (int pe = 0; pe < 2 && e == cudaSuccess; ++pe) {
+        e = cudaMallocHost((void**)&b->h_desc[pe], max_slots * sizeof(BatchDesc));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_prefix[pe], (max_slots + 1) * sizeof(long long));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hdr[pe], sizeof(BatchHeader));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_err[pe], max_slots * sizeof(unsigned));
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void**)&b->h_check[pe], 4 * max_slots * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaEventCreate(&b->ev0[pe]);
+        if (e == cudaSuccess) e = cudaEventCreate(&b->ev1[pe]);
+        if (e == cudaSuccess) e = cudaEventCreate(&b->ev2[pe]);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_stage, 2 * b->stage_ints * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_range, 2 * max_slots * sizeof(long long));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_range, 2 * max_slots * sizeof(long long));
-    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, max_slots * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -324,9 +372,11 @@ extern "C" fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
         delete b;
         return st;
     }
-    std::memset(b->h_desc, 0, max_slots * sizeof(BatchDesc));
-    std::memset(b->h_prefix, 0, (max_slots + 1) * sizeof(long long));
-    std::memset(b->h_hdr, 0, sizeof(BatchHeader));
+    for (int pe = 0; pe < 2; ++pe) {
+        std::memset(b->h_desc[pe], 0, max_slots * sizeof(BatchDesc));
+        std::memset(b->h_prefix[pe], 0, (max_slots + 1) * sizeof(long long));
+        std::memset(b->h_hdr[pe], 0, sizeof(BatchHeader));
+    }
     b->free_blocks[0] = b->budget;
     *out = b;
     return FQNM_OK;
@@ -336,9 +386,28 @@ extern "C" fqnm_status fqnm_batch_destroy(fqnm_batch* b)
 {
     if (!b) return FQNM_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->side) cudaStreamSynchronize(b->side);
     batch_free_device(b);
     delete b;
     return FQNM_OK;
+}
+
+static fqnm_status retire_oldest(fqnm_batch* b);
+
+// Retire every enqueued epoch (the plan's graphs can then be rebuilt).
+static fqnm_status drain(fqnm_batch* b)
+{
+    while (!b->inflight.empty()) {
+        fqnm_status st = retire_oldest(b);
+        if (st != FQNM_OK) return st;
+    }
+    return FQNM_OK;
+}
+
+static void drop_graphs(fqnm_batch* b)
+{
+    for (int pe = 0; pe < 2; ++pe)
+        if (b->gexec[pe]) { cudaGraphExecDestroy(b->gexec[pe]); b->gexec[pe] = nullptr; }
 }
 
 extern "C" fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
@@ -356,9 +425,11 @@ extern "C" fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, 
                          p.v, p.block, p.k, p.layout);
     // the plan only decides how each epoch cuts problems into tiles, so it
     // may change between epochs
+    fqnm_status st = drain(b);
+    if (st != FQNM_OK) return st;
     b->plan = p;
     b->tuning = false;
-    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    drop_graphs(b);
     return FQNM_OK;
 }
 
@@ -367,26 +438,36 @@ extern "C" fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan)
     if (!b) return set_error(FQNM_ERR_ARG, "null handle");
     if (epochs_per_plan < 1 || epochs_per_plan > 64)
         return set_error(FQNM_ERR_ARG, "epochs_per_plan must be 1..64");
+    fqnm_status st = drain(b);
+    if (st != FQNM_OK) return st;
     b->cands.clear();
     const int vs[2] = {8, 16}, blocks[3] = {32, 128, 256}, ks[3] = {32, 64, 128};
     RuleView dummy{};
-    for (int v : vs)
-        for (int bl : blocks)
-            for (int k : ks) {
-                Plan p;
-                p.kernel = 2; p.layout = LAYOUT_BLOCKED; p.v = v; p.block = bl; p.k = k;
-                if (4LL * k > (long long)bl * v) continue;      // > 50 % halo work
-                if (tb_plan_supported(dummy, p)) b->cands.push_back(p);
-            }
+    for (int L : {LAYOUT_BLOCKED, LAYOUT_RUNS8})
+        for (int v : vs)
+            for (int bl : blocks)
+                for (int k : ks) {
+                    Plan p;
+                    p.kernel = 2; p.layout = L; p.v = v; p.block = bl; p.k = k;
+                    if (4LL * k > (long long)bl * v) continue;      // > 50 % halo work
+                    if (tb_plan_supported(dummy, p) && batch_kernel(v, L, bl))
+                        b->cands.push_back(p);
+                }
     b->cand_ns.assign(b->cands.size(), 0.0);
     b->cand_updates.assign(b->cands.size(), 0);
-    b->tune_epoch = 0;
+    b->cand_retired.assign(b->cands.size(), 0);
+    b->tune_launch = 0;
     b->tune_per_plan = epochs_per_plan;
     b->tuning = !b->cands.empty();
-    if (b->tuning) {
-        b->plan = b->cands[0];
-        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-    }
+    if (b->tuning) b->plan = b->cands[0];
+    return FQNM_OK;
+}
+
+extern "C" fqnm_status fqnm_batch_set_margin(fqnm_batch* b, int64_t margin)
+{
+    if (!b) return set_error(FQNM_ERR_ARG, "null handle");
+    if (margin < 0 || margin > (INT32_MAX / 8)) return set_error(FQNM_ERR_ARG, "margin out of range");
+    b->margin = margin;
     return FQNM_OK;
 }
 
@@ -439,6 +520,7 @@ extern "C" fqnm_status fqnm_batch_submit(fqnm_batch* b, const fqnm_problem_spec*
     r.q0.assign(q0, q0 + n);
     r.steps = steps;
     r.arrival_ns = arrival_ns ? arrival_ns : now_ns();
+    r.margin = b->margin;
     auto mm = std::minmax_element(r.q0.begin(), r.q0.end());
     r.qmin = *mm.first;
     r.qmax = *mm.second;
@@ -469,6 +551,7 @@ extern "C" fqnm_status fqnm_batch_submit_device(fqnm_batch* b, const fqnm_proble
     r.out_dev = out;
     r.steps = steps;
     r.arrival_ns = arrival_ns ? arrival_ns : now_ns();
+    r.margin = b->margin;
     *id = (int64_t)b->reqs.size();
     b->reqs.push_back(std::move(r));
     b->queue.push_back(*id);
@@ -477,7 +560,8 @@ extern "C" fqnm_status fqnm_batch_submit_device(fqnm_batch* b, const fqnm_proble
 
 // Phase 1 of admission: a slot, the state buffers and the initial state on
 // the device; a device submission also gets its state range from the GPU.
-static fqnm_status admit_state(fqnm_batch* b, int64_t rid, size_t* stage_used, bool* admitted)
+static fqnm_status admit_state(fqnm_batch* b, int64_t rid, int32_t* stage_base,
+                               size_t* stage_used, bool* admitted)
 {
     *admitted = false;
     Request& r = b->reqs[rid];
@@ -498,17 +582,20 @@ static fqnm_status admit_state(fqnm_batch* b, int64_t rid, size_t* stage_used, b
     s.q[0] = (int32_t*)(b->arena + off);
     s.q[1] = (int32_t*)(b->arena + off + sb);
     if (host) {
-        int32_t* stage = b->h_stage + *stage_used;
+        int32_t* stage = stage_base + *stage_used;
         std::memcpy(stage, r.q0.data(), n * sizeof(int32_t));
         *stage_used += n;
         BCK(cudaMemcpyAsync(s.q[0], stage, n * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
     } else {
+        // on the side stream: the host waits for the range without waiting
+        // for the epoch in flight (the copy is complete before the state is
+        // first stepped: that wait precedes the launch)
         BCK(cudaMemcpyAsync(s.q[0], r.q0_dev, n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
-                            b->stream));
+                            b->side));
         init_minmax(b->h_range + 2 * si);
         BCK(cudaMemcpyAsync(b->d_range + 2 * si, b->h_range + 2 * si, 2 * sizeof(long long),
-                            cudaMemcpyHostToDevice, b->stream));
-        BCK(launch_minmax_i32(s.q[0], (int64_t)n, b->d_range + 2 * si, b->stream));
+                            cudaMemcpyHostToDevice, b->side));
+        BCK(launch_minmax_i32(s.q[0], (int64_t)n, b->d_range + 2 * si, b->side));
         s.range_pending = true;
     }
     r.state = 1;
@@ -578,9 +665,10 @@ static void release_slot(fqnm_batch* b, int si)
     b->free_slots.push_back(si);
 }
 
-static fqnm_status build_epoch_graph(fqnm_batch* b)
+static fqnm_status build_epoch_graph(fqnm_batch* b, int pe)
 {
     BatchKernel kern = batch_kernel(b->plan.v, b->plan.layout, b->plan.block);
+    if (!kern) return set_error(FQNM_ERR_ARG, "no batched kernel for this plan");
     int per_sm = 0, sms = 0, dev = 0;
     BCK(cudaGetDevice(&dev));
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -590,12 +678,12 @@ static fqnm_status build_epoch_graph(fqnm_batch* b)
     BCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_desc, b->h_desc, b->max_slots * sizeof(BatchDesc),
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_desc, b->h_desc[pe], b->max_slots * sizeof(BatchDesc),
                                               cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_prefix, b->h_prefix,
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_prefix, b->h_prefix[pe],
                                               (b->max_slots + 1) * sizeof(long long),
                                               cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_hdr, b->h_hdr, sizeof(BatchHeader),
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_hdr, b->h_hdr[pe], sizeof(BatchHeader),
                                               cudaMemcpyHostToDevice, cap);
     if (e == cudaSuccess) {
         kern<<<b->grid, b->plan.block, 0, cap>>>(b->d_desc, b->d_prefix, b->d_hdr);
@@ -605,9 +693,10 @@ static fqnm_status build_epoch_graph(fqnm_batch* b)
     cudaStreamDestroy(cap);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_error(e, "batch graph capture"); }
     if (ee != cudaSuccess) return cuda_error(ee, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    e = cudaGraphInstantiate(&b->gexec[pe], g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) { b->gexec = nullptr; return cuda_error(e, "cudaGraphInstantiate"); }
+    if (e != cudaSuccess) { b->gexec[pe] = nullptr; return cuda_error(e, "cudaGraphInstantiate"); }
+    b->graph_plan[pe] = b->plan;
     return FQNM_OK;
 }
 
@@ -622,13 +711,16 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
     return st;
 }
 
-static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
+static bool same_plan(const Plan& a, const Plan& b)
 {
-    *did_work = false;
+    return a.layout == b.layout && a.v == b.v && a.block == b.block && a.k == b.k;
+}
+
+// Admission: arrived requests into free slots (states first, then, after
+// the state range of device submissions is known, their tables).
+static fqnm_status admit_arrivals(fqnm_batch* b, int32_t* stage_base, size_t* stage_used)
+{
     const uint64_t t = now_ns();
-    // 1. admission: states first, then (after one sync if a device
-    // submission needs its range) the tables
-    size_t stage_used = 0;
     std::vector<int> fresh;
     bool need_range = false;
     for (auto it = b->queue.begin(); it != b->queue.end();) {
@@ -636,7 +728,7 @@ static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
         if (r.arrival_ns > t) { ++it; continue; }
         bool adm = false;
         const int64_t rid = *it;
-        fqnm_status st = admit_state(b, rid, &stage_used, &adm);
+        fqnm_status st = admit_state(b, rid, stage_base, stage_used, &adm);
         if (st != FQNM_OK) return st;
         if (adm) {
             it = b->queue.erase(it);
@@ -653,8 +745,8 @@ static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
     }
     if (need_range) {
         BCK(cudaMemcpyAsync(b->h_range, b->d_range, 2 * b->max_slots * sizeof(long long),
-                            cudaMemcpyDeviceToHost, b->stream));
-        BCK(cudaStreamSynchronize(b->stream));
+                            cudaMemcpyDeviceToHost, b->side));
+        BCK(cudaStreamSynchronize(b->side));
     }
     // tables in admission order; when one does not fit, the state blocks of
     // the later fresh requests are given back first (so that they cannot
@@ -692,26 +784,56 @@ static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
     for (auto it = requeue.rbegin(); it != requeue.rend(); ++it) b->queue.push_front(*it);
     // nothing on the device and an arrived request still waiting: it cannot
     // be admitted at all (report it rather than spin)
-    if (b->free_slots.size() == (size_t)b->max_slots) {
+    if (b->free_slots.size() == (size_t)b->max_slots && b->inflight.empty()) {
         for (int64_t rid : b->queue)
             if (b->reqs[rid].arrival_ns <= t)
                 return set_error(FQNM_ERR_OOM, "request %lld cannot be admitted into an empty "
                                  "batch (budget %zu bytes)", (long long)rid, b->budget);
     }
-    // 2. the epoch's launch over every active problem with steps left
+    return FQNM_OK;
+}
+
+// Enqueue the next epoch: one batched launch over every active problem with
+// steps left, the copies of the states that this launch finishes (or that
+// finished earlier and still wait for staging room), and the read-back of
+// the error words and rule checks.  Nothing is enqueued when there is
+// nothing to do.
+static fqnm_status launch_epoch(fqnm_batch* b, int32_t* stage_base, size_t stage_used,
+                                bool* launched)
+{
+    *launched = false;
+    const long long ep = b->next_epoch;
+    const int pe = (int)(ep & 1);
+    Inflight f;
+    f.epoch = ep;
+    f.t0 = now_ns();
+    if (b->tuning) {
+        const int c = b->tune_launch / b->tune_per_plan;
+        if (c < (int)b->cands.size()) {
+            b->plan = b->cands[c];
+            f.cand = c;
+        }
+    }
     const long long E = (long long)b->plan.block * b->plan.v;
+    BatchDesc* hd = b->h_desc[pe];
+    long long* hp = b->h_prefix[pe];
     int np = 0;
     long long total = 0;
+    bool pending = false;
     for (int si = 0; si < b->max_slots; ++si) {
         Slot& s = b->slots[si];
         s.k_this_epoch = 0;
-        if (s.req < 0) continue;
+        if (s.req < 0 || s.restarting) continue;
         Request& r = b->reqs[s.req];
-        if (s.done >= r.steps) continue;
+        if (s.check_pending && s.check_epoch < 0) pending = true;
+        if (s.done >= r.steps) {
+            if (s.finish_epoch < 0) pending = true;       // its copy still to enqueue
+            continue;
+        }
         const int k = (int)std::min<uint64_t>((uint64_t)b->plan.k, r.steps - s.done);
         const long long S = E - 2LL * k;
         const long long n = (long long)r.n;
-        BatchDesc& d = b->h_desc[np];
+        BatchDesc& d = hd[np];
         d.qin = s.q[s.cur];
         d.qout = s.q[1 - s.cur];
         d.n = n;
@@ -726,95 +848,120 @@ static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
         d.tabp = s.tabp;
         d.err = b->d_err + si;
         d.cf = s.cf;
-        b->h_prefix[np] = total;
+        hp[np] = total;
         total += (n + S - 1) / S;
         s.k_this_epoch = k;
+        f.updates += (uint64_t)k * (uint64_t)n;
         ++np;
     }
-    b->h_prefix[np] = total;
-    b->h_hdr->nprob = np;
-    b->h_hdr->total_tiles = total;
+    if (np == 0 && !pending) return FQNM_OK;
+    hp[np] = total;
+    b->h_hdr[pe]->nprob = np;
+    b->h_hdr[pe]->total_tiles = total;
+    f.np = np;
     if (np > 0) {
-        if (!b->gexec) {
-            fqnm_status st = build_epoch_graph(b);
+        // this parity's graph was last used two epochs ago (retired)
+        if (b->gexec[pe] && !same_plan(b->graph_plan[pe], b->plan)) {
+            cudaGraphExecDestroy(b->gexec[pe]);
+            b->gexec[pe] = nullptr;
+        }
+        if (!b->gexec[pe]) {
+            fqnm_status st = build_epoch_graph(b, pe);
             if (st != FQNM_OK) return st;
         }
-        BCK(cudaEventRecord(b->ev0, b->stream));
-        BCK(cudaGraphLaunch(b->gexec, b->stream));
-        BCK(cudaEventRecord(b->ev1, b->stream));
+        BCK(cudaEventRecord(b->ev0[pe], b->stream));
+        BCK(cudaGraphLaunch(b->gexec[pe], b->stream));
+        BCK(cudaEventRecord(b->ev1[pe], b->stream));
         note_launches();
         b->launches += 1;
         b->epochs += 1;
-        *did_work = true;
+        if (f.cand >= 0) b->tune_launch += 1;
     }
-    // 3. bookkeeping, copies of finished states, error words, rule checks
+    // bookkeeping; final states out
     size_t out_used = stage_used;
-    std::vector<int> finished;
     for (int si = 0; si < b->max_slots; ++si) {
         Slot& s = b->slots[si];
-        if (s.req < 0) continue;
+        if (s.req < 0 || s.restarting) continue;
         Request& r = b->reqs[s.req];
         if (s.k_this_epoch) {
             s.done += s.k_this_epoch;
             s.cur = 1 - s.cur;
+            if (s.first_epoch < 0) s.first_epoch = ep;
+            s.last_epoch = ep;
             b->cell_updates += (uint64_t)s.k_this_epoch * r.n;
         }
-        if (s.done >= r.steps && r.out_dev) {
+        if (s.check_pending && s.check_epoch < 0) s.check_epoch = ep;
+        if (s.done < r.steps || s.finish_epoch >= 0) continue;
+        if (r.out_dev) {
             BCK(cudaMemcpyAsync(r.out_dev, s.q[s.cur], r.n * sizeof(int32_t),
                                 cudaMemcpyDeviceToDevice, b->stream));
-            finished.push_back(si);
-        } else if (s.done >= r.steps && out_used + r.n <= b->stage_ints) {
-            BCK(cudaMemcpyAsync(b->h_stage + out_used, s.q[s.cur], r.n * sizeof(int32_t),
+            s.finish_epoch = ep;
+        } else if (out_used + r.n <= b->stage_ints) {
+            BCK(cudaMemcpyAsync(stage_base + out_used, s.q[s.cur], r.n * sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, b->stream));
-            finished.push_back(si);
+            s.finish_epoch = ep;
             s.out_off = out_used;
             out_used += r.n;
         }
-        *did_work = *did_work || s.req >= 0;
     }
-    BCK(cudaMemcpyAsync(b->h_err, b->d_err, b->max_slots * sizeof(unsigned),
+    BCK(cudaMemcpyAsync(b->h_err[pe], b->d_err, b->max_slots * sizeof(unsigned),
                         cudaMemcpyDeviceToHost, b->stream));
-    BCK(cudaMemcpyAsync(b->h_check, b->d_check, 4 * b->max_slots * sizeof(unsigned long long),
+    BCK(cudaMemcpyAsync(b->h_check[pe], b->d_check, 4 * b->max_slots * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost, b->stream));
-    BCK(cudaStreamSynchronize(b->stream));
+    BCK(cudaEventRecord(b->ev2[pe], b->stream));
+    b->inflight.push_back(f);
+    b->next_epoch += 1;
+    *launched = true;
+    return FQNM_OK;
+}
+
+// Wait for the oldest enqueued epoch and act on what it read back: GPU time
+// and tuning, rule checks, errors (restart the problem once no enqueued
+// epoch uses it), finished states (results, slots freed).
+static fqnm_status retire_oldest(fqnm_batch* b)
+{
+    if (b->inflight.empty()) return FQNM_OK;
+    const Inflight f = b->inflight.front();
+    b->inflight.pop_front();
+    const int pe = (int)(f.epoch & 1);
+    BCK(cudaEventSynchronize(b->ev2[pe]));
     const uint64_t tdone = now_ns();
-    if (np > 0) {
+    if (f.np > 0) {
         float ms = 0.0f;
-        BCK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        BCK(cudaEventElapsedTime(&ms, b->ev0[pe], b->ev1[pe]));
         b->gpu_ms += ms;
-        if (b->tuning) {
-            uint64_t upd = 0;
-            for (int i = 0; i < np; ++i) upd += (uint64_t)b->h_desc[i].n * b->h_desc[i].k;
-            const size_t c = (size_t)(b->tune_epoch / b->tune_per_plan);
-            b->cand_ns[c] += (double)(tdone - t);
-            b->cand_updates[c] += upd;
-            ++b->tune_epoch;
-            const size_t nc = (size_t)(b->tune_epoch / b->tune_per_plan);
-            if (nc >= b->cands.size()) {           // all tried: keep the fastest
-                size_t best = 0;
-                double best_v = 1e300;
-                for (size_t j = 0; j < b->cands.size(); ++j) {
-                    if (!b->cand_updates[j]) continue;
-                    const double v = b->cand_ns[j] / (double)b->cand_updates[j];
-                    if (v < best_v) { best_v = v; best = j; }
-                }
-                b->plan = b->cands[best];
-                b->tuning = false;
-            } else if (nc != c) {
-                b->plan = b->cands[nc];
+    }
+    // tuning: each candidate is scored by the wall time between retirements
+    // (the epoch period the host sees, its own work included) per cell update
+    const uint64_t period = tdone - (b->last_retire_ns > f.t0 ? b->last_retire_ns : f.t0);
+    b->last_retire_ns = tdone;
+    if (b->tuning && f.cand >= 0) {
+        b->cand_ns[f.cand] += (double)period;
+        b->cand_updates[f.cand] += f.updates;
+        b->cand_retired[f.cand] += 1;
+        bool all = true;
+        for (size_t j = 0; j < b->cands.size(); ++j)
+            all = all && b->cand_retired[j] >= b->tune_per_plan;
+        if (all) {                                   // all tried: keep the fastest
+            size_t best = 0;
+            double best_v = 1e300;
+            for (size_t j = 0; j < b->cands.size(); ++j) {
+                if (!b->cand_updates[j]) continue;
+                const double v = b->cand_ns[j] / (double)b->cand_updates[j];
+                if (v < best_v) { best_v = v; best = j; }
             }
-            if (b->gexec && (nc != c || !b->tuning)) {
-                cudaGraphExecDestroy(b->gexec);
-                b->gexec = nullptr;
-            }
+            b->plan = b->cands[best];
+            b->tuning = false;
         }
     }
-    // rule checks of newly admitted problems
+    const unsigned* herr = b->h_err[pe];
+    const unsigned long long* hcheck = b->h_check[pe];
+    // rule checks read back by this epoch
     for (int si = 0; si < b->max_slots; ++si) {
         Slot& s = b->slots[si];
-        if (s.req < 0 || !s.check_pending) continue;
+        if (s.req < 0 || !s.check_pending || s.check_epoch != f.epoch) continue;
         s.check_pending = false;
-        const unsigned long long* c = b->h_check + 4 * si;
+        const unsigned long long* c = hcheck + 4 * si;
         s.has_m = (c[1] & CERT_M_NONZERO) != 0;
         if (b->pack16 && c[2] <= 32767 && c[3] <= 32767) {   // both maps fit int16
             BCK(launch_pack_tab16(s.tab2, (int64_t)s.span + 1, s.tab16, b->stream));
@@ -822,30 +969,65 @@ static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
         }
         if (s.cf_candidate && c[0] == 0 && !s.has_m) s.evaluator = EVAL_CLOSED_FORM;
     }
-    // errors restart that problem alone from its initial state (wider map)
+    // errors: the problem restarts from its initial state with a wider map
     for (int si = 0; si < b->max_slots; ++si) {
         Slot& s = b->slots[si];
-        if (s.req < 0 || b->h_err[si] == 0) continue;
+        // (an error word read back before this problem's first epoch may
+        // still be its slot's previous occupant's)
+        if (s.req < 0 || s.restarting || herr[si] == 0 || s.first_epoch < 0 ||
+            f.epoch < s.first_epoch)
+            continue;
         Request& r = b->reqs[s.req];
-        if (b->h_err[si] & ERRBIT_OVERFLOW)
+        if (herr[si] & ERRBIT_OVERFLOW)
             return set_error(FQNM_ERR_OVERFLOW, "problem %lld: a transfer does not fit int32",
                              (long long)s.req);
-        finished.erase(std::remove(finished.begin(), finished.end(), si), finished.end());
         r.margin = std::max<int64_t>(4 * r.margin, 4096);
-        r.state = 0;
-        b->queue.push_front(s.req);
-        release_slot(b, si);
-        BCK(cudaMemsetAsync(b->d_err + si, 0, sizeof(unsigned), b->stream));
+        s.restarting = true;
     }
-    for (int si : finished) {
+    for (int si = 0; si < b->max_slots; ++si) {
         Slot& s = b->slots[si];
+        if (s.req < 0) continue;
         Request& r = b->reqs[s.req];
-        if (!r.out_dev) r.result.assign(b->h_stage + s.out_off, b->h_stage + s.out_off + r.n);
+        if (s.restarting) {
+            if (s.last_epoch > f.epoch) continue;     // an enqueued epoch still steps it
+            r.state = 0;
+            b->queue.push_front(s.req);
+            release_slot(b, si);
+            BCK(cudaMemsetAsync(b->d_err + si, 0, sizeof(unsigned), b->stream));
+            continue;
+        }
+        if (s.finish_epoch != f.epoch) continue;
+        if (!r.out_dev) {
+            const int32_t* stage = b->h_stage + (size_t)pe * b->stage_ints + s.out_off;
+            r.result.assign(stage, stage + r.n);
+        }
         r.done_ns = tdone;
         r.state = 2;
         b->completed.push_back(s.req);
         release_slot(b, si);
     }
+    return FQNM_OK;
+}
+
+// One epoch: admit, enqueue epoch e, then retire epoch e-1 while e runs
+// (with nothing to enqueue, retire what is in flight).
+static fqnm_status run_epoch_body(fqnm_batch* b, bool* did_work)
+{
+    *did_work = false;
+    const int pe = (int)(b->next_epoch & 1);
+    int32_t* stage_base = b->h_stage + (size_t)pe * b->stage_ints;
+    size_t stage_used = 0;
+    fqnm_status st = admit_arrivals(b, stage_base, &stage_used);
+    if (st != FQNM_OK) return st;
+    bool launched = false;
+    st = launch_epoch(b, stage_base, stage_used, &launched);
+    if (st != FQNM_OK) return st;
+    if (b->inflight.size() > 1 || (!launched && !b->inflight.empty())) {
+        st = retire_oldest(b);
+        if (st != FQNM_OK) return st;
+        *did_work = true;
+    }
+    *did_work = *did_work || launched;
     return FQNM_OK;
 }
 

@@ -693,9 +693,12 @@ static void replan(fqnm_solver* s)
     // neighbours stay mostly in the thread (1.89e12 against 1.78e12 cell
     // updates/s for 8 cells per lane, blocked, 4 warps); a closed form has no
     // gather, and the blocked layout's two shuffles per lane and step win
-    p.layout = s->opt_layout ? s->opt_layout : (table ? LAYOUT_RUNS8 : LAYOUT_BLOCKED);
-    p.v = s->opt_v ? s->opt_v : (table ? 16 : 8);
-    p.block = s->opt_block ? s->opt_block : (table ? 64 : 128);
+    // (a line of fewer than 2^18 cells fills few tiles; there the shorter
+    // per-step latency of 8 cells per lane and 4-warp blocks wins)
+    const bool runs = table && s->n >= ((size_t)1 << 18);
+    p.layout = s->opt_layout ? s->opt_layout : (runs ? LAYOUT_RUNS8 : LAYOUT_BLOCKED);
+    p.v = s->opt_v ? s->opt_v : (runs ? 16 : 8);
+    p.block = s->opt_block ? s->opt_block : (runs ? 64 : 128);
     p.k = s->opt_k ? s->opt_k : 64;
     if (p.layout == LAYOUT_RUNS8 && p.v < 16) p.layout = LAYOUT_BLOCKED;
     if (p.layout == LAYOUT_RUNS4 && p.v < 8) p.layout = LAYOUT_BLOCKED;

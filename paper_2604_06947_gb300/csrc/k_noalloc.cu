@@ -8,7 +8,8 @@
 // device), and services that must not grow their device footprint after
 // start-up.  This variant of the invariants reduction keeps its scratch -- the
 // per-block partial sums and the three totals -- in one file-scope static
-// device array, reserved on every GPU that loads the library until the
+// device array, reserved on every GPU where the library's device code is
+// loaded (under lazy module loading, at the first call there) until the
 // process exits, and allocates nothing per call.
 //
 // Limits and sharing:

@@ -138,6 +138,7 @@ PROTOTYPES = {
     "fqnm_batch_destroy": (_st, [_vp]),
     "fqnm_batch_set_plan": (_st, [_vp, C.c_int, C.c_int, C.c_int, C.c_int]),
     "fqnm_batch_autotune": (_st, [_vp, C.c_int]),
+    "fqnm_batch_set_margin": (_st, [_vp, C.c_int64]),
     "fqnm_batch_get_plan": (_st, [_vp] + [C.POINTER(C.c_int)] * 5),
     "fqnm_batch_submit": (_st, [_vp, C.POINTER(fqnm_problem_spec), _vp, C.c_size_t,
                                 C.c_uint64, C.c_uint64, C.POINTER(C.c_int64)]),
@@ -588,6 +589,10 @@ def fqnm_batch_set_plan(b: int, cells_per_thread: int = 0, block: int = 0, k: in
 
 def fqnm_batch_autotune(b: int, epochs_per_plan: int = 3):
     _check(load().fqnm_batch_autotune(b, epochs_per_plan))
+
+
+def fqnm_batch_set_margin(b: int, margin: int):
+    _check(load().fqnm_batch_set_margin(b, int(margin)))
 
 
 def fqnm_batch_get_plan(b: int) -> dict:

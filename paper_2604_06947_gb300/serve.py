@@ -69,7 +69,7 @@ def serve_batched(requests: List[I.ServeRequest], q0s=None,
                   budget_bytes: int = 16 << 30, max_slots: int = 1024,
                   plan: Optional[dict] = None, keep: Optional[set] = None,
                   lead_s: float = 0.02, dev: Optional[DeviceStream] = None,
-                  deadline_s: float = 600.0) -> dict:
+                  deadline_s: float = 600.0, margin: Optional[int] = None) -> dict:
     """Run the stream through one batch in real time.
 
     q0s: host initial states (host submission), or dev: a DeviceStream whose
@@ -78,6 +78,8 @@ def serve_batched(requests: List[I.ServeRequest], q0s=None,
     """
     b = F.fqnm_batch_create(budget_bytes, max_slots)
     try:
+        if margin is not None:
+            F.fqnm_batch_set_margin(b, margin)
         if plan == "autotune":
             F.fqnm_batch_autotune(b, 3)
         elif plan:

@@ -104,6 +104,38 @@ def test_large_problems_in_the_mix(orc):
         assert np.array_equal(bat["results"][i], one["results"][i])
 
 
+def test_range_escapes_restart_inside_the_pipeline(orc):
+    """Maps built with no margin around an under-dissipative Burgers split
+    (alpha = 1 against max|u| = 1.3: states leave their initial range): each
+    escape is seen one epoch late, with the next epoch already enqueued, and
+    restarts only that problem with a wider map; every result still equals
+    the oracle's, next to ordinary requests in the same stream."""
+    base = small_stream(n_requests=10, seed=31)
+    reqs = []
+    for i, rq in enumerate(base):
+        p = I.materialise(rq)
+        if i % 3 == 0:                                   # the escaping problems
+            e = I.burgers_problem(n=4096, steps=600 + 100 * i, seed=6 + i)
+            e.alpha, e.dt = 1.0, 0.4 * e.dx
+            p = e
+        reqs.append(I.ServeRequest(rq.rid, rq.arrival_s, p, rq.data_seed))
+    q0s = [F.fqnm_quantise(rq.problem.u0, rq.problem.delta) for rq in reqs]
+    # the same escape on the single-problem path (it recovers there too)
+    e = reqs[0].problem
+    s = F.Solver.for_problem(e, margin=0).load(q0s[0])
+    s.step(e.steps)
+    F.fqnm_sync(s.h)
+    assert F.fqnm_get_rule(s.h)["recoveries"] >= 1
+    s.close()
+    bat = S.serve_batched(reqs, q0s, budget_bytes=64 << 20, max_slots=4, margin=0,
+                          plan=dict(cells_per_thread=8, block=128, k=16, layout=2))
+    for i, rq in enumerate(reqs):
+        p = rq.problem
+        want = orc.step(orc.quantise(p.u0, p.delta), p.flux, p.delta, p.dx, p.dt, p.steps,
+                        a=p.a, alpha=p.alpha)
+        assert np.array_equal(bat["results"][i].astype(np.int64), want), i
+
+
 def test_tight_budget_admits_one_at_a_time():
     """A budget that holds one problem's tables at a time (and the states of
     several): admission must still make progress, in order."""
