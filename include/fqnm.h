@@ -520,12 +520,14 @@ fqnm_status fqnm_batch_destroy(fqnm_batch* b);
  * first); results do not depend on it. */
 fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
                                 int k, int layout);
-/* Autotune the plan online: the next epochs with work try each candidate
- * (blocked or runs of 8 cells, cells per thread 8/16, 32/128/256 threads, K
- * 32/64/128, halo work at most half the tile) for epochs_per_plan epochs,
- * then keep the one with the least wall time between epoch retirements per
- * cell update (the host's admission and bookkeeping overlap the GPU's
- * epochs, so this is the period the stream sees). */
+/* Autotune the plan online: the next epochs with work try the candidates
+ * in turn (blocked or runs of 8 cells, cells per thread 8/16, 32/128/256
+ * threads, K 32/64/128, halo work at most half the tile), epochs_per_plan
+ * epochs each, and keep the one with the least wall time between epoch
+ * retirements per time step (the wait of an active problem per step, the
+ * epoch's fixed costs included; the host's admission and bookkeeping
+ * overlap the GPU's epochs).  The default plan is blocked, 8 cells per
+ * thread, 128 threads, K = 128. */
 fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan);
 /* The quanta added on each side of a request's state range when its
  * transfer maps are built (default 1024), for requests submitted after this

@@ -192,6 +192,7 @@ struct Inflight {                    // an enqueued epoch not yet retired
     uint64_t updates = 0;            // cell updates it performs
     uint64_t t0 = 0;                 // host clock when it was enqueued
     int cand = -1;                   // autotuning candidate it runs, or -1
+    int k = 1;                       // steps per problem in this epoch (the plan's K)
 };
 
 }  // namespace
@@ -240,13 +241,14 @@ struct fqnm_batch {
     // plan
     Plan plan;
     int grid = 0;
-    // online autotuning: candidate plans tried on the first epochs with work,
-    // scored by the epochs' wall time (host admission, replay and sync
-    // included: a fixed cost per epoch that small K pays more often) per
-    // cell update
+    // online autotuning: candidate plans tried in turn (round robin, so that
+    // each sees the same mix of load) on the first epochs with work, scored
+    // by the wall time between epoch retirements per time step: the time an
+    // active problem waits for each of its steps, fixed costs per epoch
+    // included (a long-running request's latency is its steps times this)
     bool tuning = false;
     std::vector<Plan> cands;
-    std::vector<double> cand_ns;             // wall ns of the epochs, summed
+    std::vector<double> cand_ns;             // wall ns per time step, summed over epochs
     std::vector<uint64_t> cand_updates;
     std::vector<int> cand_retired;
     int tune_launch = 0, tune_per_plan = 3;
@@ -336,7 +338,7 @@ extern "C" fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
     b->plan.layout = LAYOUT_BLOCKED;
     b->plan.v = 8;
     b->plan.block = 128;
-    b->plan.k = 32;
+    b->plan.k = 128;
     b->stage_ints = (size_t)32 << 20;                 // 2 x 128 MiB pinned staging
     cudaError_t e = cudaSuccess;
     if (stream) b->stream = (cudaStream_t)stream;
@@ -808,12 +810,14 @@ static fqnm_status launch_epoch(fqnm_batch* b, int32_t* stage_base, size_t stage
     f.epoch = ep;
     f.t0 = now_ns();
     if (b->tuning) {
-        const int c = b->tune_launch / b->tune_per_plan;
-        if (c < (int)b->cands.size()) {
+        const int nc = (int)b->cands.size();
+        if (b->tune_launch < nc * b->tune_per_plan) {
+            const int c = b->tune_launch % nc;
             b->plan = b->cands[c];
             f.cand = c;
         }
     }
+    f.k = b->plan.k;
     const long long E = (long long)b->plan.block * b->plan.v;
     BatchDesc* hd = b->h_desc[pe];
     long long* hp = b->h_prefix[pe];
@@ -932,11 +936,11 @@ static fqnm_status retire_oldest(fqnm_batch* b)
         b->gpu_ms += ms;
     }
     // tuning: each candidate is scored by the wall time between retirements
-    // (the epoch period the host sees, its own work included) per cell update
+    // (the epoch period the host sees, its own work included) per time step
     const uint64_t period = tdone - (b->last_retire_ns > f.t0 ? b->last_retire_ns : f.t0);
     b->last_retire_ns = tdone;
-    if (b->tuning && f.cand >= 0) {
-        b->cand_ns[f.cand] += (double)period;
+    if (b->tuning && f.cand >= 0 && f.np > 0) {
+        b->cand_ns[f.cand] += (double)period / (double)f.k;
         b->cand_updates[f.cand] += f.updates;
         b->cand_retired[f.cand] += 1;
         bool all = true;
@@ -946,8 +950,8 @@ static fqnm_status retire_oldest(fqnm_batch* b)
             size_t best = 0;
             double best_v = 1e300;
             for (size_t j = 0; j < b->cands.size(); ++j) {
-                if (!b->cand_updates[j]) continue;
-                const double v = b->cand_ns[j] / (double)b->cand_updates[j];
+                if (!b->cand_retired[j]) continue;
+                const double v = b->cand_ns[j] / (double)b->cand_retired[j];
                 if (v < best_v) { best_v = v; best = j; }
             }
             b->plan = b->cands[best];
