@@ -387,6 +387,31 @@ def test_degenerate_inputs(orc, kernel):
     s.close()
 
 
+@pytest.mark.parametrize("plan", [{}, dict(layout=2, cells_per_thread=8, block=128, k=64),
+                                  dict(layout=4, cells_per_thread=16, block=64, k=128)])
+def test_range_escape_on_a_long_line(orc, plan):
+    """The same overshoot on 2^18 cells (the runs-of-8 default and two other
+    tiled plans, CUDA-graph replay): the escape is reported, the map widened
+    and the run replayed from its checkpoint, bit-exact; with recovery off
+    it is a status."""
+    p = I.burgers_problem(n=1 << 18, steps=0, seed=6)
+    p.alpha = 1.0
+    p.dt = 0.4 * p.dx / p.alpha
+    q0 = gpu_q0(p)
+    want = orc.step(q0.astype(np.int64), p.flux, p.delta, p.dx, p.dt, 1000, alpha=p.alpha)
+    s = F.Solver.for_problem(p, margin=0, **plan)
+    s.load(q0).step(1000)
+    assert np.array_equal(s.state().astype(np.int64), want)
+    assert s.rule()["recoveries"] >= 1
+    s.close()
+    s = F.Solver.for_problem(p, margin=0, recover=0, **plan)
+    s.load(q0).step(1000)
+    with pytest.raises(F.FqnmError) as e:
+        F.fqnm_sync(s.h)
+    assert e.value.status == -3
+    s.close()
+
+
 def test_range_escape_without_recovery_is_a_status(orc):
     p = escaping_problem()
     s = F.Solver.for_problem(p, margin=0, recover=0)
