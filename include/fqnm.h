@@ -526,8 +526,11 @@ fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
  * epochs each, and keep the one with the least wall time between epoch
  * retirements per time step (the wait of an active problem per step, the
  * epoch's fixed costs included; the host's admission and bookkeeping
- * overlap the GPU's epochs).  The default plan is blocked, 8 cells per
- * thread, 128 threads, K = 128. */
+ * overlap the GPU's epochs).  Candidates are timed only on epochs that step
+ * at least 16 problems (the first epochs of a stream, with a few small
+ * problems, would favour the smallest tiles); until then the current plan
+ * runs.  The default plan is blocked, 8 cells per thread, 128 threads,
+ * K = 128. */
 fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan);
 /* The quanta added on each side of a request's state range when its
  * transfer maps are built (default 1024), for requests submitted after this

@@ -8,8 +8,8 @@
 //      smaller ones behind it), copies their initial states to the device
 //      and builds their transfer maps there (eq. flux_table, as a single
 //      solver would);
-//   2. replays a CUDA graph that uploads the table of active problems and
-//      launches one persistent batched kernel: every tile of every active
+//   2. uploads the table of active problems (one copy of the bytes in use)
+//      and launches one persistent batched kernel: every tile of every active
 //      problem runs the same temporal-blocked tile code as the single-problem
 //      kernel, advancing that problem by min(K, remaining) steps;
 //   3. copies finished states to host memory, frees their memory and slots,
@@ -186,6 +186,8 @@ struct Slot {
     bool restarting = false;         // an error was seen: restart once no epoch uses it
 };
 
+constexpr int TUNE_MIN_ACTIVE = 16;  // problems stepping before tuning epochs count
+
 struct Inflight {                    // an enqueued epoch not yet retired
     long long epoch = 0;
     int np = 0;                      // problems it steps
@@ -210,24 +212,28 @@ struct fqnm_batch {
     std::deque<int64_t> queue;
     std::deque<int64_t> completed;            // finished, not yet reported
     // device
-    BatchDesc* d_desc = nullptr;
-    long long* d_prefix = nullptr;
-    BatchHeader* d_hdr = nullptr;
-    unsigned* d_err = nullptr;
-    unsigned long long* d_check = nullptr;
+    // the epoch's problem table, packed as [header | tile prefix (np+1) |
+    // descriptors (np)] and uploaded in one copy of just the bytes in use
+    char* d_tab = nullptr;
+    size_t tab_bytes = 0;
+    // error words and rule-check results, read back in one copy (the check
+    // part only when a check is due)
+    char* d_rb = nullptr;
+    size_t rb_err_bytes = 0, rb_bytes = 0;
+    unsigned* d_err = nullptr;                // into d_rb
+    unsigned long long* d_check = nullptr;    // into d_rb
     long long* d_range = nullptr;             // [2*slot]: min, max of a device submission
     cudaStream_t side = nullptr;              // device submissions' state ranges
     double gpu_ms = 0.0;
-    // per epoch parity (two epochs in flight): pinned descriptor tables and
-    // read-backs, the graph that uploads the tables and launches the kernel,
-    // and the events around it; the staging area is split in two halves
-    BatchDesc* h_desc[2] = {nullptr, nullptr};
-    long long* h_prefix[2] = {nullptr, nullptr};
-    BatchHeader* h_hdr[2] = {nullptr, nullptr};
-    unsigned* h_err[2] = {nullptr, nullptr};
-    unsigned long long* h_check[2] = {nullptr, nullptr};
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    Plan graph_plan[2];
+    // per epoch parity (two epochs in flight): the pinned problem table and
+    // read-back buffer and the events around the launch; the staging area
+    // is split in two halves
+    char* h_tab[2] = {nullptr, nullptr};
+    std::vector<BatchDesc> desc_scratch;
+    std::vector<long long> prefix_scratch;
+    char* h_rb[2] = {nullptr, nullptr};
+    Plan grid_plan;                           // the plan `grid` was sized for
+    bool grid_valid = false;
     // ev0 / ev1 bracket the batched launch (GPU time); ev2 follows the
     // epoch's copies and read-backs (its retirement waits on it)
     cudaEvent_t ev0[2] = {nullptr, nullptr}, ev1[2] = {nullptr, nullptr}, ev2[2] = {nullptr, nullptr};
@@ -252,6 +258,7 @@ struct fqnm_batch {
     std::vector<uint64_t> cand_updates;
     std::vector<int> cand_retired;
     int tune_launch = 0, tune_per_plan = 3;
+    Plan tune_default;                       // the plan run while tuning waits for load
     // counters
     uint64_t launches = 0, cell_updates = 0, epochs = 0;
     bool pack16 = false;                     // packed int16 tables (off: faster on GB300)
@@ -261,22 +268,15 @@ struct fqnm_batch {
 static void batch_free_device(fqnm_batch* b)
 {
     for (int pe = 0; pe < 2; ++pe) {
-        if (b->gexec[pe]) cudaGraphExecDestroy(b->gexec[pe]);
         if (b->ev0[pe]) cudaEventDestroy(b->ev0[pe]);
         if (b->ev1[pe]) cudaEventDestroy(b->ev1[pe]);
         if (b->ev2[pe]) cudaEventDestroy(b->ev2[pe]);
-        cudaFreeHost(b->h_desc[pe]);
-        cudaFreeHost(b->h_prefix[pe]);
-        cudaFreeHost(b->h_hdr[pe]);
-        cudaFreeHost(b->h_err[pe]);
-        cudaFreeHost(b->h_check[pe]);
+        cudaFreeHost(b->h_tab[pe]);
+        cudaFreeHost(b->h_rb[pe]);
     }
     cudaFree(b->arena);
-    cudaFree(b->d_desc);
-    cudaFree(b->d_prefix);
-    cudaFree(b->d_hdr);
-    cudaFree(b->d_err);
-    cudaFree(b->d_check);
+    cudaFree(b->d_tab);
+    cudaFree(b->d_rb);
     cudaFree(b->d_range);
     cudaFreeHost(b->h_range);
     cudaFreeHost(b->h_stage);
@@ -345,18 +345,19 @@ extern "C" fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
     else { e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking); b->own_stream = true; }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->arena, b->budget);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, max_slots * sizeof(BatchDesc));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_prefix, (max_slots + 1) * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_hdr, sizeof(BatchHeader));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, max_slots * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_check, 4 * max_slots * sizeof(unsigned long long));
+    b->tab_bytes = align_up(sizeof(BatchHeader) + (max_slots + 1) * sizeof(long long), 16) +
+                   max_slots * sizeof(BatchDesc);
+    b->rb_err_bytes = align_up(max_slots * sizeof(unsigned), 16);
+    b->rb_bytes = b->rb_err_bytes + 4 * max_slots * sizeof(unsigned long long);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tab, b->tab_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_rb, b->rb_bytes);
+    if (e == cudaSuccess) {
+        b->d_err = (unsigned*)b->d_rb;
+        b->d_check = (unsigned long long*)(b->d_rb + b->rb_err_bytes);
+    }
     for (int pe = 0; pe < 2 && e == cudaSuccess; ++pe) {
-        e = cudaMallocHost((void**)&b->h_desc[pe], max_slots * sizeof(BatchDesc));
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_prefix[pe], (max_slots + 1) * sizeof(long long));
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hdr[pe], sizeof(BatchHeader));
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_err[pe], max_slots * sizeof(unsigned));
-        if (e == cudaSuccess)
-            e = cudaMallocHost((void**)&b->h_check[pe], 4 * max_slots * sizeof(unsigned long long));
+        e = cudaMallocHost((void**)&b->h_tab[pe], b->tab_bytes);
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_rb[pe], b->rb_bytes);
         if (e == cudaSuccess) e = cudaEventCreate(&b->ev0[pe]);
         if (e == cudaSuccess) e = cudaEventCreate(&b->ev1[pe]);
         if (e == cudaSuccess) e = cudaEventCreate(&b->ev2[pe]);
@@ -364,7 +365,7 @@ extern "C" fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_stage, 2 * b->stage_ints * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_range, 2 * max_slots * sizeof(long long));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_range, 2 * max_slots * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, max_slots * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_rb, 0, b->rb_bytes, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         fqnm_status st = (e == cudaErrorMemoryAllocation)
@@ -375,9 +376,8 @@ extern "C" fqnm_status fqnm_batch_create(size_t mem_budget_bytes, int max_slots,
         return st;
     }
     for (int pe = 0; pe < 2; ++pe) {
-        std::memset(b->h_desc[pe], 0, max_slots * sizeof(BatchDesc));
-        std::memset(b->h_prefix[pe], 0, (max_slots + 1) * sizeof(long long));
-        std::memset(b->h_hdr[pe], 0, sizeof(BatchHeader));
+        std::memset(b->h_tab[pe], 0, b->tab_bytes);
+        std::memset(b->h_rb[pe], 0, b->rb_bytes);
     }
     b->free_blocks[0] = b->budget;
     *out = b;
@@ -396,7 +396,7 @@ extern "C" fqnm_status fqnm_batch_destroy(fqnm_batch* b)
 
 static fqnm_status retire_oldest(fqnm_batch* b);
 
-// Retire every enqueued epoch (the plan's graphs can then be rebuilt).
+// Retire every enqueued epoch (before the plan changes).
 static fqnm_status drain(fqnm_batch* b)
 {
     while (!b->inflight.empty()) {
@@ -406,10 +406,9 @@ static fqnm_status drain(fqnm_batch* b)
     return FQNM_OK;
 }
 
-static void drop_graphs(fqnm_batch* b)
+static void drop_grid(fqnm_batch* b)
 {
-    for (int pe = 0; pe < 2; ++pe)
-        if (b->gexec[pe]) { cudaGraphExecDestroy(b->gexec[pe]); b->gexec[pe] = nullptr; }
+    b->grid_valid = false;
 }
 
 extern "C" fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, int block,
@@ -431,7 +430,7 @@ extern "C" fqnm_status fqnm_batch_set_plan(fqnm_batch* b, int cells_per_thread, 
     if (st != FQNM_OK) return st;
     b->plan = p;
     b->tuning = false;
-    drop_graphs(b);
+    drop_grid(b);
     return FQNM_OK;
 }
 
@@ -461,7 +460,7 @@ extern "C" fqnm_status fqnm_batch_autotune(fqnm_batch* b, int epochs_per_plan)
     b->tune_launch = 0;
     b->tune_per_plan = epochs_per_plan;
     b->tuning = !b->cands.empty();
-    if (b->tuning) b->plan = b->cands[0];
+    b->tune_default = b->plan;
     return FQNM_OK;
 }
 
@@ -667,38 +666,25 @@ static void release_slot(fqnm_batch* b, int si)
     b->free_slots.push_back(si);
 }
 
-static fqnm_status build_epoch_graph(fqnm_batch* b, int pe)
+static bool same_plan(const Plan& a, const Plan& b)
 {
-    BatchKernel kern = batch_kernel(b->plan.v, b->plan.layout, b->plan.block);
-    if (!kern) return set_error(FQNM_ERR_ARG, "no batched kernel for this plan");
+    return a.layout == b.layout && a.v == b.v && a.block == b.block && a.k == b.k;
+}
+
+// The batched kernel's grid for the current plan: every SM filled with as
+// many blocks as it holds (the kernel loops over the epoch's tiles).
+static fqnm_status size_grid(fqnm_batch* b, BatchKernel* kern)
+{
+    *kern = batch_kernel(b->plan.v, b->plan.layout, b->plan.block);
+    if (!*kern) return set_error(FQNM_ERR_ARG, "no batched kernel for this plan");
+    if (b->grid_valid && same_plan(b->grid_plan, b->plan)) return FQNM_OK;
     int per_sm = 0, sms = 0, dev = 0;
     BCK(cudaGetDevice(&dev));
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->plan.block, 0));
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, *kern, b->plan.block, 0));
     b->grid = std::max(1, per_sm) * sms;
-    cudaStream_t cap = nullptr;
-    BCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_desc, b->h_desc[pe], b->max_slots * sizeof(BatchDesc),
-                                              cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_prefix, b->h_prefix[pe],
-                                              (b->max_slots + 1) * sizeof(long long),
-                                              cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_hdr, b->h_hdr[pe], sizeof(BatchHeader),
-                                              cudaMemcpyHostToDevice, cap);
-    if (e == cudaSuccess) {
-        kern<<<b->grid, b->plan.block, 0, cap>>>(b->d_desc, b->d_prefix, b->d_hdr);
-        e = cudaGetLastError();
-    }
-    cudaError_t ee = cudaStreamEndCapture(cap, &g);
-    cudaStreamDestroy(cap);
-    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_error(e, "batch graph capture"); }
-    if (ee != cudaSuccess) return cuda_error(ee, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&b->gexec[pe], g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { b->gexec[pe] = nullptr; return cuda_error(e, "cudaGraphInstantiate"); }
-    b->graph_plan[pe] = b->plan;
+    b->grid_plan = b->plan;
+    b->grid_valid = true;
     return FQNM_OK;
 }
 
@@ -713,10 +699,6 @@ static fqnm_status run_epoch(fqnm_batch* b, bool* did_work)
     return st;
 }
 
-static bool same_plan(const Plan& a, const Plan& b)
-{
-    return a.layout == b.layout && a.v == b.v && a.block == b.block && a.k == b.k;
-}
 
 // Admission: arrived requests into free slots (states first, then, after
 // the state range of device submissions is known, their tables).
@@ -810,17 +792,32 @@ static fqnm_status launch_epoch(fqnm_batch* b, int32_t* stage_base, size_t stage
     f.epoch = ep;
     f.t0 = now_ns();
     if (b->tuning) {
+        // candidates are timed only under load (at least TUNE_MIN_ACTIVE
+        // problems stepping): the first epochs of a stream, with a handful of
+        // small problems, would favour the smallest tiles
+        int active = 0;
+        for (int si = 0; si < b->max_slots; ++si) {
+            const Slot& s = b->slots[si];
+            active += s.req >= 0 && !s.restarting && s.done < b->reqs[s.req].steps;
+        }
         const int nc = (int)b->cands.size();
-        if (b->tune_launch < nc * b->tune_per_plan) {
+        if (active >= TUNE_MIN_ACTIVE && b->tune_launch < nc * b->tune_per_plan) {
             const int c = b->tune_launch % nc;
             b->plan = b->cands[c];
             f.cand = c;
+        } else {
+            b->plan = b->tune_default;
         }
     }
     f.k = b->plan.k;
     const long long E = (long long)b->plan.block * b->plan.v;
-    BatchDesc* hd = b->h_desc[pe];
-    long long* hp = b->h_prefix[pe];
+    // descriptors first into a staging order, packed after the prefix below
+    std::vector<BatchDesc>& hdv = b->desc_scratch;
+    hdv.resize(b->max_slots);
+    BatchDesc* hd = hdv.data();
+    std::vector<long long>& hpv = b->prefix_scratch;
+    hpv.resize(b->max_slots + 1);
+    long long* hp = hpv.data();
     int np = 0;
     long long total = 0;
     bool pending = false;
@@ -860,21 +857,29 @@ static fqnm_status launch_epoch(fqnm_batch* b, int32_t* stage_base, size_t stage
     }
     if (np == 0 && !pending) return FQNM_OK;
     hp[np] = total;
-    b->h_hdr[pe]->nprob = np;
-    b->h_hdr[pe]->total_tiles = total;
     f.np = np;
     if (np > 0) {
-        // this parity's graph was last used two epochs ago (retired)
-        if (b->gexec[pe] && !same_plan(b->graph_plan[pe], b->plan)) {
-            cudaGraphExecDestroy(b->gexec[pe]);
-            b->gexec[pe] = nullptr;
-        }
-        if (!b->gexec[pe]) {
-            fqnm_status st = build_epoch_graph(b, pe);
-            if (st != FQNM_OK) return st;
-        }
+        BatchKernel kern = nullptr;
+        fqnm_status st = size_grid(b, &kern);
+        if (st != FQNM_OK) return st;
+        // this parity's pinned table was last read by the copy of epoch
+        // ep - 2, which has been retired
+        char* h = b->h_tab[pe];
+        BatchHeader hdr{};
+        hdr.nprob = np;
+        hdr.total_tiles = total;
+        std::memcpy(h, &hdr, sizeof(hdr));
+        const size_t off_prefix = sizeof(BatchHeader);
+        const size_t off_desc = align_up(off_prefix + (size_t)(np + 1) * sizeof(long long), 16);
+        std::memcpy(h + off_prefix, hp, (size_t)(np + 1) * sizeof(long long));
+        std::memcpy(h + off_desc, hd, (size_t)np * sizeof(BatchDesc));
+        const size_t bytes = off_desc + (size_t)np * sizeof(BatchDesc);
         BCK(cudaEventRecord(b->ev0[pe], b->stream));
-        BCK(cudaGraphLaunch(b->gexec[pe], b->stream));
+        BCK(cudaMemcpyAsync(b->d_tab, h, bytes, cudaMemcpyHostToDevice, b->stream));
+        kern<<<b->grid, b->plan.block, 0, b->stream>>>(
+            (const BatchDesc*)(b->d_tab + off_desc), (const long long*)(b->d_tab + off_prefix),
+            (const BatchHeader*)b->d_tab);
+        BCK(cudaGetLastError());
         BCK(cudaEventRecord(b->ev1[pe], b->stream));
         note_launches();
         b->launches += 1;
@@ -908,9 +913,12 @@ static fqnm_status launch_epoch(fqnm_batch* b, int32_t* stage_base, size_t stage
             out_used += r.n;
         }
     }
-    BCK(cudaMemcpyAsync(b->h_err[pe], b->d_err, b->max_slots * sizeof(unsigned),
-                        cudaMemcpyDeviceToHost, b->stream));
-    BCK(cudaMemcpyAsync(b->h_check[pe], b->d_check, 4 * b->max_slots * sizeof(unsigned long long),
+    // one read-back: the error words, and the rule checks when one is due
+    bool checks = false;
+    for (int si = 0; si < b->max_slots && !checks; ++si)
+        checks = b->slots[si].req >= 0 && b->slots[si].check_pending &&
+                 b->slots[si].check_epoch == ep;
+    BCK(cudaMemcpyAsync(b->h_rb[pe], b->d_rb, checks ? b->rb_bytes : b->rb_err_bytes,
                         cudaMemcpyDeviceToHost, b->stream));
     BCK(cudaEventRecord(b->ev2[pe], b->stream));
     b->inflight.push_back(f);
@@ -958,8 +966,8 @@ static fqnm_status retire_oldest(fqnm_batch* b)
             b->tuning = false;
         }
     }
-    const unsigned* herr = b->h_err[pe];
-    const unsigned long long* hcheck = b->h_check[pe];
+    const unsigned* herr = (const unsigned*)b->h_rb[pe];
+    const unsigned long long* hcheck = (const unsigned long long*)(b->h_rb[pe] + b->rb_err_bytes);
     // rule checks read back by this epoch
     for (int si = 0; si < b->max_slots; ++si) {
         Slot& s = b->slots[si];
