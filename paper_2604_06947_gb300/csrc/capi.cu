@@ -605,8 +605,11 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
         return set_error(FQNM_ERR_OVERFLOW, "a transfer-map value does not fit int32");
     const unsigned long long flags = s->h_check[1];
     const long long maxp = (long long)s->h_check[2], maxm = (long long)s->h_check[3];
-    // one step from inside [lo, hi] must not overflow int32
-    if (hi + 2 * (maxp + maxm) >= INT32_MAX || lo - 2 * (maxp + maxm) <= INT32_MIN)
+    // one step from inside [lo, hi] must not overflow int32: an update moves a
+    // state by at most 2 d (max|phi+| + max|phi-|) on a d-D grid (the d-D
+    // kernels sum in int32 and rely on this)
+    const long long reach = 2LL * std::max(1, s->grid.d) * (maxp + maxm);
+    if (hi + reach >= INT32_MAX || lo - reach <= INT32_MIN)
         return set_error(FQNM_ERR_OVERFLOW, "state range too close to the int32 limits");
 
     RuleView r{};

@@ -6,9 +6,12 @@
 //   F_{i+e_m/2} = phi+(q_i) + phi-(q_{i+e_m})
 //   q_i <- q_i - sum_m (F_{i+e_m/2} - F_{i-e_m/2})
 //        = q_i - d (phi+(q_i) - phi-(q_i)) + sum_m (phi+(q_{i-e_m}) - phi-(q_{i+e_m})).
-// Two kernels: one step per launch with warps walking the slowest axis
-// (2-D and 3-D), and K steps per launch in register tiles (2-D).  Updates
-// are summed in 64-bit and checked against int32.
+// Kernels: one step per launch with warps walking the slowest axis (2-D and
+// 3-D; 3-D by streaming z slabs), K steps per launch in register tiles
+// (2-D) and K steps per launch by pipelined walks (2-D and 3-D).  The
+// marching kernels sum updates in 64-bit and check them against int32; the
+// others sum in int32, which the rule build makes exact by refusing a range
+// within 2 d (max|phi+| + max|phi-|) of the int32 limits.
 #include "nd.h"
 #include "tile_step.cuh"
 
@@ -223,6 +226,113 @@ k_march3d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, lon
     if (over) atomicOr(err, ERRBIT_OVERFLOW);
 }
 
+// ---- streaming one-step 3-D kernel ---------------------------------------------
+// A warp owns STREAM_OWN = 30 consecutive x on R consecutive y rows and walks
+// a chunk of z slabs.  Its 32 lanes hold columns x0-1 .. x0+30 (lanes 1..30
+// update; lanes 0 and 31 supply the x neighbours by shuffle), and each lane
+// also evaluates the row below and the row above its R rows, so the y
+// neighbours stay in the thread.  No shared memory and no barrier: the warps
+// are independent.  While slab z is updated, slab z+2's maps are evaluated
+// and slab z+3's states loaded, so two slabs of loads and gathers are in
+// flight per warp.  The update is summed in int32: the rule build checks
+// that one d-D step from inside the table's range cannot overflow, and a
+// state outside that range is a range error anyway (its maps are clamped).
+constexpr int STREAM_OWN = 30;
+
+template <class Ev, int R>
+__global__ void __launch_bounds__(128)
+k_stream3d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long long ny,
+           long long nz, long long strips, long long rowblocks, long long zlen, long long items,
+           Ev ev, unsigned* __restrict__ err)
+{
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= items) return;                                  // whole warps
+    const int lane = threadIdx.x & 31;
+    const long long strip = wid % strips, rb = (wid / strips) % rowblocks;
+    const long long zc = wid / (strips * rowblocks);
+    const long long xu = strip * STREAM_OWN - 1 + lane;        // unwrapped column
+    const long long x = tb::wrap_index(xu, nx);
+    const long long y0 = rb * R;
+    const long long sz = nx * ny;
+    int yo[R + 2];                                             // rows y0-1 .. y0+R
+#pragma unroll
+    for (int r = 0; r < R + 2; ++r) yo[r] = (int)(tb::wrap_index(y0 - 1 + r, ny) * nx);
+    const long long z0 = zc * zlen, z1 = z0 + zlen < nz ? z0 + zlen : nz;
+    const bool xown = lane >= 1 && lane <= STREAM_OWN && xu < nx;
+    unsigned acc = 0;
+    auto load = [&](long long z, int (&q)[R + 2]) {
+        const int* b = qin + tb::wrap_index(z, nz) * sz + x;
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) q[r] = __ldg(b + yo[r]);
+    };
+    auto eval = [&](const int (&q)[R + 2], int (&p)[R + 2], int (&m)[R + 2]) {
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) ev(q[r], p[r], m[r], acc);
+    };
+    int pp[R];                                                 // p of slab z-1, rows 0..R-1
+    int qc[R + 2], pc[R + 2], mc[R + 2];                       // slab z
+    int qn[R + 2], pn[R + 2], mn[R + 2];                       // slab z+1
+    int qf[R + 2];                                             // slab z+2, loaded
+    {
+        int qd[R + 2], pd[R + 2], md[R + 2];
+        load(z0 - 1, qd);
+        load(z0, qc);
+        load(z0 + 1, qn);
+        load(z0 + 2, qf);
+        eval(qd, pd, md);
+        eval(qc, pc, mc);
+        eval(qn, pn, mn);
+#pragma unroll
+        for (int r = 0; r < R; ++r) pp[r] = pd[r + 1];
+    }
+    for (long long z = z0; z < z1; ++z) {
+        int qg[R + 2], pf[R + 2], mf[R + 2];
+        if (z + 3 <= z1) load(z + 3, qg);                      // slab z+3: needed from z+2 on
+        if (z + 2 <= z1) eval(qf, pf, mf);                     // slab z+2's maps
+#pragma unroll
+        for (int r = 0; r < R; ++r) {                          // update slab z, row y0 + r
+            const int pcr = pc[r + 1], mcr = mc[r + 1];
+            const int pl = __shfl_up_sync(0xffffffffu, pcr, 1);     // x - 1
+            const int mr = __shfl_down_sync(0xffffffffu, mcr, 1);   // x + 1
+            const int v = qc[r + 1] - 3 * (pcr - mcr) + pl + pc[r] + pp[r] - mr - mc[r + 2]
+                          - mn[r + 1];
+            const long long o = z * sz + (long long)yo[r + 1] + x;
+            if (xown && y0 + r < ny && FQNM_IN_RANGE(o, nz * sz, err)) qout[o] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) pp[r] = pc[r + 1];
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) {
+            qc[r] = qn[r]; pc[r] = pn[r]; mc[r] = mn[r];
+            qn[r] = qf[r]; pn[r] = pf[r]; mn[r] = mf[r];
+            qf[r] = qg[r];
+        }
+    }
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+}
+
+constexpr int STREAM_R = 8;
+
+template <class Ev>
+cudaError_t launch_stream3d(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
+                            unsigned* err, cudaStream_t st)
+{
+    const long long nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    const long long strips = (nx + STREAM_OWN - 1) / STREAM_OWN;
+    const long long rowblocks = (ny + STREAM_R - 1) / STREAM_R;
+    // z chunks: about 64 slabs each (the pipeline's three extra slabs per
+    // chunk cost under 5 %), more when the grid is shallow in z
+    const long long zlen = std::min<long long>(nz, 64);
+    const long long chunks = (nz + zlen - 1) / zlen;
+    const long long items = strips * rowblocks * chunks;
+    const long long blocks = (items * 32 + 127) / 128;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_stream3d<Ev, STREAM_R><<<(unsigned)blocks, 128, 0, st>>>(qin, qout, nx, ny, nz, strips,
+                                                               rowblocks, zlen, items, ev, err);
+    note_launches();
+    return cudaGetLastError();
+}
+
 template <class Ev>
 cudaError_t dispatch_march(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
                            unsigned* err, cudaStream_t st)
@@ -235,6 +345,8 @@ cudaError_t dispatch_march(const Ev& ev, const int32_t* qin, int32_t* qout, cons
         const long long blocks = (warps + 7) / 8;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
         k_march2d<<<(unsigned)blocks, 256, 0, st>>>(qin, qout, nx, ny, strips, chunks, ev, err);
+    } else if (nx * ny < (1LL << 31)) {
+        return launch_stream3d(ev, qin, qout, g, err, st);
     } else {
         const long long rowblocks = (ny + MARCH3_ROWS - 1) / MARCH3_ROWS;
         const long long zchunks = (nz + MARCH3_SLABS - 1) / MARCH3_SLABS;
