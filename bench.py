@@ -669,14 +669,17 @@ def sod_large(F, torch, stream, finals, n=1 << 20, window=20_000):
 
 def nd_workload(F, torch, stream, dims, steps):
     """Burgers on a periodic 2-D or 3-D grid (directional composition):
-    device-timed steps, the default plan, other K-step plans and the one-step
-    kernel."""
+    device-timed steps, the default plan (2-D: the walk at K = 4; 3-D: the
+    one-step streaming kernel), the autotuned plan, other plans and the
+    two-word (unpacked) map table."""
     p = I.burgers_nd_problem(dims, steps=steps)
     u0 = torch.from_numpy(p.u0).cuda()
     out = {"dims": list(dims), "n_cells": p.n, "time_steps": steps}
     plans = [("default", {}), ("autotuned", {"autotune": 1})] + (
-        [("tile_64x32", {"nd_tile": 3}), ("one_step", {"kernel": 1})] if len(dims) == 2 else
-        [("walk_k1", {"k": 1}), ("walk_k3", {"k": 3}), ("one_step", {"kernel": 1})])
+        [("tile_64x32", {"nd_tile": 3}), ("one_step", {"kernel": 1}),
+         ("two_word_table", {"pack16": 0})] if len(dims) == 2 else
+        [("walk_k1", {"k": 1}), ("walk_k2", {"k": 2}), ("walk_k3", {"k": 3}),
+         ("two_word_table", {"pack16": 0})])
     for name, opt in plans:
         s = F.Solver.for_problem(p, **opt)
         s.set_grid(p.dims)

@@ -164,15 +164,17 @@ typedef enum {
     FQNM_OPT_RECOVER = 7,    /* 1 (default): on range escape widen the map and replay */
     FQNM_OPT_AUTOTUNE = 8,   /* 1: time candidate plans at load and keep the fastest: 1-D
                                 temporal-blocked plans (cached per size class), or on a
-                                grid the walk depths and (2-D) register tiles, unless a d-D
-                                plan option (FQNM_OPT_ND_TILE, FQNM_OPT_K) was set */
+                                grid the walk depths, (2-D) the register tiles and (3-D) the
+                                one-step kernel, unless a d-D plan option (FQNM_OPT_ND_TILE,
+                                FQNM_OPT_K) was set */
     FQNM_OPT_GRAPH = 9,      /* 1 (default): replay long step loops from a CUDA graph */
     FQNM_OPT_PDL = 10,       /* 1 (default): chain step launches with programmatic dependent
                                 launch (the next launch's blocks start while the previous
                                 drains, and wait for its results before reading them) */
     FQNM_OPT_PACK16 = 11,    /* 1: when |phi+-| < 2^15 on the range, gather both maps from one
                                 32-bit word (half the table footprint, two more instructions
-                                per cell; 0, the default, is faster while the table fits L1/L2) */
+                                per cell); 0: never; -1, the default: on d-D grids only (in 1-D
+                                the unpacked table is faster while it fits L1/L2) */
     FQNM_OPT_QUANTISE_MASK = 12, /* EULER_ROE: components evolved by integer transfer, bits
                                 1 rho, 2 m, 4 E (default 7, componentwise).  1 is the density-
                                 channel prototype of §3.3: m and E evolve in double with the
@@ -184,9 +186,10 @@ typedef enum {
                                 (K in 1, 2, 3, 4, 6, 8; others round down); 1..5 register tiles
                                 of x by y cells, 1 64x64, 2 128x64, 3 64x32, 4 128x32, 5 32x128
                                 (K below half the smaller side).  FQNM_OPT_KERNEL = 1 selects one
-                                step per launch.  3-D grids take K steps per launch (K in 1..4,
-                                default 2) by blocks of rows walking z; FQNM_OPT_KERNEL = 1
-                                selects one step per launch there too. */,
+                                step per launch.  3-D grids take one step per launch by
+                                default (warps streaming z slabs), or, when FQNM_OPT_K is set
+                                or this option is 6, K steps per launch (K in 1..4, default 2)
+                                by blocks of rows walking z. */,
     FQNM_OPT_VERIFY = 14,    /* 1: at each synchronising call, check that every integer
                                 variable's total plus its counted boundary transfer still
                                 equals its value at load (eq. exact_conservation holds for

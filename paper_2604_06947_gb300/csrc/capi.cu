@@ -192,7 +192,7 @@ struct fqnm_solver {
     int32_t* tabp = nullptr;
     int32_t* tab16 = nullptr;
     int64_t tab_cap = 0;
-    int pack16 = 0;                        // option: pack the maps as int16 pairs
+    int pack16 = -1;                       // option: pack the maps as int16 pairs (-1 auto)
     RuleView rule{};
     fqnm_rule_info info{};
 
@@ -479,7 +479,7 @@ extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value
     case FQNM_OPT_RECOVER: s->recover = value != 0; break;
     case FQNM_OPT_AUTOTUNE: s->autotune = value != 0; break;
     case FQNM_OPT_GRAPH: s->use_graph = value != 0; break;
-    case FQNM_OPT_PACK16: s->pack16 = value != 0; break;
+    case FQNM_OPT_PACK16: s->pack16 = value < 0 ? -1 : value != 0; break;
     case FQNM_OPT_VERIFY: {
         s->verify = value != 0;
         if (s->verify && s->loaded) {            // expect the totals as they stand now
@@ -617,7 +617,9 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
     r.tabp = s->tabp;
     r.tab16 = nullptr;
     // both maps fit int16: the packed table halves the gather footprint
-    if (s->pack16 && maxp <= 32767 && maxm <= 32767) {
+    // (by default on d-D grids, whose gathers miss L1 more often)
+    const bool pack = s->pack16 > 0 || (s->pack16 < 0 && s->grid.d > 1);
+    if (pack && maxp <= 32767 && maxm <= 32767) {
         CK(launch_pack_tab16(s->tab2, count, s->tab16, s->stream));
         r.tab16 = s->tab16;
     }
@@ -792,11 +794,12 @@ static void write_tune_file()
     std::rename(tmp.c_str(), path);
 }
 
-// d-D plans: every walk depth the kernels support and (2-D) every register
-// tile at K = 2, 3, 4, each timed twice (interleaved) over about 32 steps
-// that evolve scratch copies of the loaded state.  The default plan (the
-// walk at K = 4 in 2-D, 2 in 3-D) stays unless another is more than 3 %
-// faster per step: short timings on a large grid drift by about that much.
+// d-D plans: every walk depth the kernels support, (2-D) every register
+// tile at K = 2, 3, 4 and (3-D) the one-step streaming kernel, each timed
+// twice (interleaved) over about 32 steps that evolve scratch copies of the
+// loaded state.  The default plan (the walk at K = 4 in 2-D, the one-step
+// kernel in 3-D) stays unless another is more than 3 % faster per step:
+// short timings on a large grid drift by about that much.
 static fqnm_status autotune_nd(fqnm_solver* s)
 {
     if (s->opt_kernel == 1 || s->opt_nd_tile != 0 || s->opt_k != 0) return FQNM_OK;
@@ -807,6 +810,7 @@ static fqnm_status autotune_nd(fqnm_solver* s)
         for (int t = 1; t <= 5; ++t)
             for (int k : {2, 3, 4}) cands.push_back({t, k});
     } else {
+        cands.push_back({0, 1});                      // one step per launch
         for (int k = 1; k <= 4; ++k) cands.push_back({ND_WALK, k});
     }
     DeviceScratch<int32_t> scratch;
@@ -817,6 +821,7 @@ static fqnm_status autotune_nd(fqnm_solver* s)
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     auto launch = [&](const Cand& c, const int32_t* in, int32_t* out) {
+        if (c.tile == 0) return launch_step_nd(s->rule, in, out, s->grid, s->d_err, s->stream);
         if (c.tile == ND_WALK)
             return s->grid.d == 3 ? launch_walk3d(s->rule, in, out, s->grid, c.k, s->d_err, s->stream)
                                   : launch_walk2d(s->rule, in, out, s->grid, c.k, s->d_err, s->stream);
@@ -848,10 +853,10 @@ static fqnm_status autotune_nd(fqnm_solver* s)
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) return cuda_error(e, "autotune_nd");
-    const int dflt_k = s->grid.d == 3 ? 2 : 4;
+    const Cand dc = s->grid.d == 3 ? Cand{0, 1} : Cand{ND_WALK, 4};
     size_t dflt = 0, pick = 0;
     for (size_t i = 0; i < cands.size(); ++i) {
-        if (cands[i].tile == ND_WALK && cands[i].k == dflt_k) dflt = i;
+        if (cands[i].tile == dc.tile && cands[i].k == dc.k) dflt = i;
         if (best[i] < best[pick]) pick = i;
     }
     if (best[pick] * 1.03f > best[dflt]) pick = dflt;
@@ -1134,19 +1139,27 @@ static bool graph_valid(const fqnm_solver* s)
            a.cf.rounding == b.cf.rounding;
 }
 
-// The d-D plan: K steps per launch (the walk, or on 2-D grids register tiles)
-// unless the one-step kernel was asked for (FQNM_OPT_KERNEL = 1).
+// The d-D plan.  2-D: K steps per launch (the walk, or register tiles)
+// unless the one-step kernel was asked for (FQNM_OPT_KERNEL = 1).  3-D: the
+// one-step kernel streaming z slabs, unless a walk was asked for (FQNM_OPT_K
+// or FQNM_OPT_ND_TILE = 6): its single pass over the grid per step beats the
+// K-step walk, whose shared-memory exchange and barrier per slab bound it.
 static NdPlan nd_plan(const fqnm_solver* s)
 {
     NdPlan p;
     p.blocked = s->opt_kernel != 1;
     // the autotuner's plan, unless a plan option was set explicitly
     if (p.blocked && s->nd_tuned_tile >= 0 && s->opt_nd_tile == 0 && s->opt_k == 0) {
+        if (s->nd_tuned_tile == 0) {                  // the one-step kernel
+            p.blocked = 0;
+            return p;
+        }
         p.walk = s->nd_tuned_tile == ND_WALK;
         if (!p.walk) p.shape = s->nd_tuned_tile;
         p.k = s->nd_tuned_k;
         return p;
     }
+    if (s->grid.d == 3 && s->opt_k == 0 && s->opt_nd_tile == 0) p.blocked = 0;
     p.walk = s->grid.d == 3 || s->opt_nd_tile == 0 || s->opt_nd_tile == ND_WALK;
     if (!p.walk) p.shape = s->opt_nd_tile;
     const int lim = s->grid.d == 3 ? 4

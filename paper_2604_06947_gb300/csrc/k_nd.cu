@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 namespace fqnm {
 
@@ -311,6 +312,102 @@ k_stream3d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, lo
     if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
 }
 
+// The same walk for the packed table (both maps as int16 halves of one
+// word): each cell's maps stay packed in one register and are unpacked where
+// they are used, so a row of the pipeline holds 8 registers instead of 11;
+// with 7 rows per warp and 32-bit offsets (a grid holds fewer than 2^31
+// cells) four blocks fit an SM.
+template <int R>
+__global__ void __launch_bounds__(128, 4)
+k_stream3d_pk(const int* __restrict__ qin, int* __restrict__ qout, int nx, int ny, int nz,
+              int strips, int rowblocks, int zlen, int items, tb::EvTablePM16 ev,
+              unsigned* __restrict__ err)
+{
+    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (wid >= items) return;                                  // whole warps
+    const int lane = threadIdx.x & 31;
+    const int strip = wid % strips, rb = (wid / strips) % rowblocks;
+    const int zc = wid / (strips * rowblocks);
+    const int xu = strip * STREAM_OWN - 1 + lane;              // unwrapped column
+    const int x = xu < 0 ? xu + nx : xu >= nx ? xu - nx : xu;  // |xu| < 2 nx
+    const int y0 = rb * R;
+    const int sz = nx * ny;
+    int yo[R + 2];                                             // rows y0-1 .. y0+R
+#pragma unroll
+    for (int r = 0; r < R + 2; ++r) {
+        int y = y0 - 1 + r;
+        y = y < 0 ? y + ny : y;
+        y = y >= ny ? y % ny : y;                              // a ragged block's rows wrap
+        yo[r] = y * nx + x;
+    }
+    const int z0 = zc * zlen, z1 = z0 + zlen < nz ? z0 + zlen : nz;
+    unsigned own = 0;                                          // bit r: row y0 + r is ours
+    if (lane >= 1 && lane <= STREAM_OWN && xu < nx) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) own |= (unsigned)(y0 + r < ny) << r;
+    }
+    unsigned acc = 0;
+    auto slab = [&](int z) { z = z < 0 ? z + nz : z; return (z >= nz ? z - nz : z) * sz; };
+    auto load = [&](int z, int (&q)[R + 2]) {
+        const int* b = qin + slab(z);
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) q[r] = __ldg(b + yo[r]);
+    };
+    auto gather = [&](const int (&q)[R + 2], int (&w)[R + 2]) {
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) {
+            const unsigned i = (unsigned)(q[r] - ev.lo);
+            acc = max(acc, i);
+            w[r] = __ldg(ev.tab + min(i, ev.span));            // never outside the table
+        }
+    };
+    auto P = [](int w) { return (int)(short)(w & 0xffff); };   // phi+: the low half
+    auto M = [](int w) { return w >> 16; };                    // phi-: the high half
+    int wp[R];                                                 // slab z-1, rows 0..R-1
+    int qc[R + 2], wc[R + 2];                                  // slab z
+    int qn[R + 2], wn[R + 2];                                  // slab z+1
+    int qf[R + 2];                                             // slab z+2, loaded
+    {
+        int qd[R + 2], wd[R + 2];
+        load(z0 - 1, qd);
+        load(z0, qc);
+        load(z0 + 1, qn);
+        load(z0 + 2, qf);
+        gather(qd, wd);
+        gather(qc, wc);
+        gather(qn, wn);
+#pragma unroll
+        for (int r = 0; r < R; ++r) wp[r] = wd[r + 1];
+    }
+    for (int z = z0; z < z1; ++z) {
+        int qg[R + 2], wf[R + 2];
+        if (z + 3 <= z1) load(z + 3, qg);                      // slab z+3: needed from z+2 on
+        if (z + 2 <= z1) gather(qf, wf);                       // slab z+2's maps
+        int* const o = qout + z * sz;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {                          // update slab z, row y0 + r
+            const int pcr = P(wc[r + 1]), mcr = M(wc[r + 1]);
+            const int pl = __shfl_up_sync(0xffffffffu, pcr, 1);     // x - 1
+            const int mr = __shfl_down_sync(0xffffffffu, mcr, 1);   // x + 1
+            const int v = qc[r + 1] - 3 * (pcr - mcr) + pl + P(wc[r]) + P(wp[r]) - mr
+                          - M(wc[r + 2]) - M(wn[r + 1]);
+            if (((own >> r) & 1) && FQNM_IN_RANGE((long long)z * sz + yo[r + 1],
+                                                  (long long)nz * sz, err))
+                o[yo[r + 1]] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) wp[r] = wc[r + 1];
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) {
+            qc[r] = qn[r]; wc[r] = wn[r];
+            qn[r] = qf[r]; wn[r] = wf[r];
+            qf[r] = qg[r];
+        }
+    }
+    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
+}
+
+constexpr int STREAM_R_PK = 7;
 constexpr int STREAM_R = 8;
 
 template <class Ev>
@@ -318,17 +415,46 @@ cudaError_t launch_stream3d(const Ev& ev, const int32_t* qin, int32_t* qout, con
                             unsigned* err, cudaStream_t st)
 {
     const long long nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    constexpr bool packed = std::is_same<Ev, tb::EvTablePM16>::value;
+    constexpr int R = packed ? STREAM_R_PK : STREAM_R;
     const long long strips = (nx + STREAM_OWN - 1) / STREAM_OWN;
-    const long long rowblocks = (ny + STREAM_R - 1) / STREAM_R;
-    // z chunks: about 64 slabs each (the pipeline's three extra slabs per
-    // chunk cost under 5 %), more when the grid is shallow in z
-    const long long zlen = std::min<long long>(nz, 64);
+    const long long rowblocks = (ny + R - 1) / R;
+    // Blocks of four warps run in waves of `slots` (the SMs times the blocks
+    // each holds), and a warp's chunk of c slabs costs c + 2 slab times (the
+    // pipeline loads and evaluates the slab below and the slab above the
+    // chunk): take the chunk length (4 slabs at least) whose waves x slab
+    // times is least.
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        if constexpr (packed)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream3d_pk<R>, 128, 0);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream3d<Ev, STREAM_R>, 128, 0);
+    }
+    if (e != cudaSuccess) return e;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    const long long cols = strips * rowblocks;
+    long long zlen = nz, best = -1;
+    for (long long c = 1; c <= nz && c <= 1024; ++c) {
+        const long long len = (nz + c - 1) / c, chunks = (nz + len - 1) / len;
+        if (len < 4 && c > 1) break;
+        const long long blocks = (cols * chunks + 3) / 4;
+        const long long cost = ((blocks + slots - 1) / slots) * (len + 2);
+        if (best < 0 || cost < best) { best = cost; zlen = len; }
+    }
     const long long chunks = (nz + zlen - 1) / zlen;
-    const long long items = strips * rowblocks * chunks;
+    const long long items = cols * chunks;
     const long long blocks = (items * 32 + 127) / 128;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_stream3d<Ev, STREAM_R><<<(unsigned)blocks, 128, 0, st>>>(qin, qout, nx, ny, nz, strips,
-                                                               rowblocks, zlen, items, ev, err);
+    if constexpr (packed)   // every count below fits int: the grid holds < 2^31 cells
+        k_stream3d_pk<R><<<(unsigned)blocks, 128, 0, st>>>(qin, qout, (int)nx, (int)ny, (int)nz,
+                                                           (int)strips, (int)rowblocks, (int)zlen,
+                                                           (int)items, ev, err);
+    else
+        k_stream3d<Ev, STREAM_R><<<(unsigned)blocks, 128, 0, st>>>(qin, qout, nx, ny, nz, strips,
+                                                                   rowblocks, zlen, items, ev, err);
     note_launches();
     return cudaGetLastError();
 }

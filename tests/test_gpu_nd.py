@@ -56,11 +56,12 @@ def test_every_2d_plan_bit_exact(orc, tile, k):
 
 
 @pytest.mark.parametrize("dims", [(100, 60), (1, 5), (31, 1), (33, 150), (64, 129), (7, 3, 2),
-                                  (40, 30, 70)])
+                                  (40, 30, 70), (30, 8, 5), (31, 9, 33), (1, 1, 6), (61, 17, 45),
+                                  (2, 50, 300)])
 def test_one_step_marching_kernel(orc, dims):
-    """The one-step kernels (2-D: warps walk y; 3-D: blocks of rows walk z)
-    on shapes narrower than a warp, with one row, with several walk chunks
-    and ragged strips."""
+    """The one-step kernels (2-D: warps walk y; 3-D: warps stream z slabs)
+    on shapes narrower than a warp, with one row, with several z chunks
+    (ragged last chunk), whole and ragged 30-column strips and 8-row blocks."""
     p = I.burgers_nd_problem(dims)
     shape = dims[::-1]
     q0 = orc.quantise(p.u0, p.delta).reshape(shape)
@@ -87,10 +88,12 @@ def test_3d_walk_bit_exact(orc, k):
         s.close()
 
 
-@pytest.mark.parametrize("opt", [{}, {"pack16": 1}])
+@pytest.mark.parametrize("opt", [{}, {"pack16": 0}, {"k": 2}, {"k": 2, "pack16": 0}])
 def test_3d_walk_evaluators(orc, opt):
-    """The 3-D walk with the verified closed form (upwind, nu = 0.3 per axis)
-    and with the table evaluators (Lax-Friedrichs split, 16-bit pack)."""
+    """The 3-D one-step kernel (default) and the walk with the verified closed
+    form (upwind, nu = 0.3 per axis) and with the table evaluators
+    (Lax-Friedrichs split, 16-bit pack by default on d-D grids, the two-word
+    table)."""
     dims = (48, 36, 30)
     shape = dims[::-1]
     p = I.burgers_nd_problem(dims)
@@ -109,14 +112,15 @@ def test_3d_walk_evaluators(orc, opt):
     s.close()
 
 
-def test_full_size_3d_grid(orc):
-    """160^3 cells, 16 steps (four launches of the walk), against the oracle;
-    exact mass."""
+@pytest.mark.parametrize("opt", [{}, {"k": 2}])
+def test_full_size_3d_grid(orc, opt):
+    """160^3 cells, 16 steps (sixteen launches of the default one-step
+    kernel, or eight of the walk at K = 2), against the oracle; exact mass."""
     dims = (160, 160, 160)
     shape = dims[::-1]
     p = I.burgers_nd_problem(dims)
     q0 = orc.quantise(p.u0, p.delta).reshape(shape)
-    s = solver_for(p).load(q0.reshape(-1))
+    s = solver_for(p, **opt).load(q0.reshape(-1))
     s.step(16)
     want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 16, alpha=p.alpha)
     assert np.array_equal(s.state().reshape(shape), want)
@@ -126,14 +130,15 @@ def test_full_size_3d_grid(orc):
 
 @pytest.mark.parametrize("dims", [(150, 70), (96, 64, 40)])
 def test_autotuned_nd_plan_bit_exact(orc, dims):
-    """The d-D autotuner's choice (walk depths and, in 2-D, register tiles,
-    timed at load) gives the oracle's states; an explicit K turns it off."""
+    """The d-D autotuner's choice (walk depths, in 2-D register tiles, in 3-D
+    the one-step kernel, timed at load) gives the oracle's states; an
+    explicit K turns it off."""
     p = I.burgers_nd_problem(dims)
     shape = dims[::-1]
     q0 = orc.quantise(p.u0, p.delta).reshape(shape)
     s = solver_for(p, autotune=1).load(q0.reshape(-1))
     st = s.stats()
-    assert st["kernel"] in ((5,) if len(dims) == 3 else (5, 6)) and st["k"] >= 1
+    assert st["kernel"] in ((1, 5) if len(dims) == 3 else (5, 6)) and st["k"] >= 1
     s.step(13)
     want = orc.step_nd(q0, "burgers_lf", p.delta, p.dx, p.dt, 13, alpha=p.alpha)
     assert np.array_equal(s.state().reshape(shape), want)
