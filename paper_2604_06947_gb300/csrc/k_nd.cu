@@ -6,12 +6,12 @@
 //   F_{i+e_m/2} = phi+(q_i) + phi-(q_{i+e_m})
 //   q_i <- q_i - sum_m (F_{i+e_m/2} - F_{i-e_m/2})
 //        = q_i - d (phi+(q_i) - phi-(q_i)) + sum_m (phi+(q_{i-e_m}) - phi-(q_{i+e_m})).
-// Kernels: one step per launch with warps walking the slowest axis (2-D and
-// 3-D; 3-D by streaming z slabs), K steps per launch in register tiles
-// (2-D) and K steps per launch by pipelined walks (2-D and 3-D).  The
-// marching kernels sum updates in 64-bit and check them against int32; the
-// others sum in int32, which the rule build makes exact by refusing a range
-// within 2 d (max|phi+| + max|phi-|) of the int32 limits.
+// Kernels: one step per launch (2-D: warps marching y; 3-D: warps streaming
+// z slabs), K steps per launch in register tiles (2-D) and K steps per
+// launch by pipelined walks (2-D and 3-D).  The 2-D marching kernel sums
+// updates in 64-bit and checks them against int32; the others sum in int32,
+// which the rule build makes exact by refusing a range within
+// 2 d (max|phi+| + max|phi-|) of the int32 limits.
 #include "nd.h"
 #include "tile_step.cuh"
 
@@ -123,97 +123,6 @@ k_march2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, lon
             if (x < nx && y + g < y1 && FQNM_IN_RANGE((y + g) * nx + x, nx * ny, err)) {
                 if (v < INT_MIN || v > INT_MAX) over = true;
                 qout[(y + g) * nx + x] = (int)v;
-            }
-        }
-        pd = pn[MARCH_G - 2];
-        qc = qn[MARCH_G - 1];
-        pc = pn[MARCH_G - 1];
-        mc = mn[MARCH_G - 1];
-        plc = pl[MARCH_G - 1];
-        mrc = mr[MARCH_G - 1];
-    }
-    if (acc > ev.span) atomicOr(err, ERRBIT_RANGE);
-    if (over) atomicOr(err, ERRBIT_OVERFLOW);
-}
-
-constexpr int MARCH3_WARPS = 16;          // 14 rows + 2 halo rows per block
-constexpr int MARCH3_ROWS = MARCH3_WARPS - 2;
-constexpr int MARCH3_SLABS = 32;          // z slabs per block; a multiple of MARCH_G
-
-template <class Ev>
-__global__ void __launch_bounds__(32 * MARCH3_WARPS)
-k_march3d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, long long ny,
-          long long nz, long long strips, long long rowblocks, Ev ev, unsigned* __restrict__ err)
-{
-    __shared__ int shp[2][MARCH3_WARPS][32];
-    __shared__ int shm[2][MARCH3_WARPS][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long b = blockIdx.x;
-    const long long strip = b % strips, rb = (b / strips) % rowblocks, zc = b / (strips * rowblocks);
-    const long long x = strip * 32 + lane;
-    const long long xc = x < nx ? x : nx - 1;
-    const EdgeCols e = edge_cols(xc, nx, lane);
-    // warp w handles row y = rb*ROWS + w - 1 (w = 0 and w = WARPS-1: halo rows)
-    long long y = rb * MARCH3_ROWS + w - 1;
-    const bool owner = w >= 1 && w <= MARCH3_ROWS && y < ny;
-    y = tb::wrap_index(y, ny);
-    const long long sy = nx, sz = nx * ny;
-    const long long z0 = zc * MARCH3_SLABS;
-    const long long z1 = z0 + MARCH3_SLABS < nz ? z0 + MARCH3_SLABS : nz;
-    unsigned acc = 0;
-    bool over = false;
-    int pd, md, qc, pc, mc, plc = 0, mrc = 0;
-    {
-        const long long zd = z0 > 0 ? z0 - 1 : nz - 1;
-        ev(__ldg(qin + zd * sz + y * sy + xc), pd, md, acc);
-        const int* row = qin + z0 * sz + y * sy;
-        qc = __ldg(row + xc);
-        ev(qc, pc, mc, acc);
-        int t;
-        if (e.need_l) ev(__ldg(row + e.xl), plc, t, acc);
-        if (e.need_r) ev(__ldg(row + e.xr), t, mrc, acc);
-    }
-    int s = 0;
-    for (long long z = z0; z < z1; z += MARCH_G) {
-        int qn[MARCH_G], pn[MARCH_G], mn[MARCH_G], pl[MARCH_G], mr[MARCH_G];
-#pragma unroll
-        for (int g = 0; g < MARCH_G; ++g) {
-            long long r = z + 1 + g;
-            if (r >= nz) r -= nz;
-            if (r >= nz) r %= nz;
-            const int* row = qin + r * sz + y * sy;
-            qn[g] = __ldg(row + xc);
-            pl[g] = e.need_l ? __ldg(row + e.xl) : 0;
-            mr[g] = e.need_r ? __ldg(row + e.xr) : 0;
-        }
-#pragma unroll
-        for (int g = 0; g < MARCH_G; ++g) {
-            int t;
-            ev(qn[g], pn[g], mn[g], acc);
-            if (e.need_l) ev(pl[g], pl[g], t, acc);
-            if (e.need_r) ev(mr[g], t, mr[g], acc);
-        }
-#pragma unroll
-        for (int g = 0; g < MARCH_G; ++g, s ^= 1) {     // update slab z+g
-            const int q0 = g == 0 ? qc : qn[g - 1];
-            const int p0 = g == 0 ? pc : pn[g - 1];
-            const int m0 = g == 0 ? mc : mn[g - 1];
-            const int pdn = g == 0 ? pd : (g == 1 ? pc : pn[g - 2]);
-            shp[s][w][lane] = p0;
-            shm[s][w][lane] = m0;
-            __syncthreads();
-            int l = __shfl_up_sync(0xffffffffu, p0, 1);
-            int r = __shfl_down_sync(0xffffffffu, m0, 1);
-            if (e.need_l) l = g == 0 ? plc : pl[g - 1];
-            if (e.need_r) r = g == 0 ? mrc : mr[g - 1];
-            if (owner) {
-                const int pdy = shp[s][w - 1][lane], muy = shm[s][w + 1][lane];
-                const long long v = (long long)q0 - 3LL * ((long long)p0 - (long long)m0) + l + pdy
-                                    + pdn - (long long)r - (long long)muy - (long long)mn[g];
-                if (x < nx && z + g < z1 && FQNM_IN_RANGE((z + g) * sz + y * sy + x, nz * sz, err)) {
-                    if (v < INT_MIN || v > INT_MAX) over = true;
-                    qout[(z + g) * sz + y * sy + x] = (int)v;
-                }
             }
         }
         pd = pn[MARCH_G - 2];
@@ -463,7 +372,7 @@ template <class Ev>
 cudaError_t dispatch_march(const Ev& ev, const int32_t* qin, int32_t* qout, const NdGrid& g,
                            unsigned* err, cudaStream_t st)
 {
-    const long long nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    const long long nx = g.dims[0], ny = g.dims[1];
     const long long strips = (nx + 31) / 32;
     if (g.d == 2) {
         const long long chunks = (ny + MARCH_ROWS - 1) / MARCH_ROWS;
@@ -471,15 +380,8 @@ cudaError_t dispatch_march(const Ev& ev, const int32_t* qin, int32_t* qout, cons
         const long long blocks = (warps + 7) / 8;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
         k_march2d<<<(unsigned)blocks, 256, 0, st>>>(qin, qout, nx, ny, strips, chunks, ev, err);
-    } else if (nx * ny < (1LL << 31)) {
-        return launch_stream3d(ev, qin, qout, g, err, st);
     } else {
-        const long long rowblocks = (ny + MARCH3_ROWS - 1) / MARCH3_ROWS;
-        const long long zchunks = (nz + MARCH3_SLABS - 1) / MARCH3_SLABS;
-        const long long blocks = strips * rowblocks * zchunks;
-        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-        k_march3d<<<(unsigned)blocks, 32 * MARCH3_WARPS, 0, st>>>(qin, qout, nx, ny, nz, strips,
-                                                                   rowblocks, ev, err);
+        return launch_stream3d(ev, qin, qout, g, err, st);
     }
     note_launches();
     return cudaGetLastError();
