@@ -197,3 +197,30 @@ def test_grid_errors():
     with pytest.raises(F.FqnmError):
         F.fqnm_set_grid(s.h, (16, 16))                   # d nu = 1.2
     s.close()
+
+
+def test_int32_headroom_scales_with_dimension():
+    """One update moves a state by at most 2 d (max|phi+| + max|phi-|), and
+    the d-D kernels sum in int32, so the rule build refuses a range closer
+    than that to the int32 limits.  Upwind with nu = 0.3 (phi+ = 0.3 q,
+    phi- = 0): a constant 8e8-quanta state passes the 1-D bound (1.6 q) but
+    not the 3-D one (2.8 q > 2^31); 7e8 passes both, and constant states
+    stay constant."""
+    p = I.burgers_nd_problem((8, 8, 8))
+    p.flux, p.a, p.alpha = "linear_upwind", 1.0, 0.0
+    p.dt = 0.3 * p.dx
+    big = np.full(p.n, 800_000_000, dtype=np.int32)
+    s = F.Solver.for_problem(p)                          # the same cells as a 1-D line
+    s.load(big).step(3)
+    assert (s.state() == big).all()
+    s.close()
+    s = solver_for(p)
+    with pytest.raises(F.FqnmError) as e:
+        s.load(big)
+    assert e.value.status == -4
+    s.close()
+    ok = np.full(p.n, 700_000_000, dtype=np.int32)
+    s = solver_for(p).load(ok)
+    s.step(3)
+    assert (s.state() == ok).all()
+    s.close()
