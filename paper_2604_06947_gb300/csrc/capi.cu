@@ -195,6 +195,10 @@ struct fqnm_solver {
     int pack16 = -1;                       // option: pack the maps as int16 pairs (-1 auto)
     RuleView rule{};
     fqnm_rule_info info{};
+    // the last rule built, reused by a load whose range and settings match:
+    // rule_gen counts the calls that can change a rule (options, grid)
+    uint64_t rule_gen = 1, built_gen = 0;
+    int64_t built_lo = 0, built_hi = -1;
 
     // device / pinned scratch
     unsigned* d_err = nullptr;
@@ -453,6 +457,7 @@ static fqnm_status set_expected_totals(fqnm_solver* s);
 extern "C" fqnm_status fqnm_set_option(fqnm_solver* s, int option, int64_t value)
 {
     if (!s) return set_error(FQNM_ERR_ARG, "null handle");
+    ++s->rule_gen;                          // the next load builds its rule afresh
     switch (option) {
     case FQNM_OPT_KERNEL:
         if (value < 0 || value > 4 || value == 3)
@@ -556,6 +561,12 @@ static fqnm_status tabulate_custom(fqnm_solver* s, int64_t lo, int64_t count)
 
 static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
 {
+    // the maps are functions of the state alone: the same range under the
+    // same settings gives the same tables, checks and closed form (custom
+    // split callbacks are tabulated again every time: they are the caller's)
+    if (s->built_gen == s->rule_gen && lo == s->built_lo && hi == s->built_hi && !s->fplus)
+        return FQNM_OK;
+    s->built_gen = 0;
     const int64_t count = hi - lo + 1;
     if (count <= 0 || count > (1ll << 30))
         return set_error(FQNM_ERR_RANGE, "transfer-map range [%lld, %lld] too large",
@@ -666,6 +677,9 @@ static fqnm_status build_rule(fqnm_solver* s, int64_t lo, int64_t hi)
     }
     s->rule = r;
     s->info = info;
+    s->built_gen = s->rule_gen;
+    s->built_lo = lo;
+    s->built_hi = hi;
     return FQNM_OK;
 }
 
@@ -1689,6 +1703,7 @@ extern "C" fqnm_status fqnm_set_grid(fqnm_solver* s, int d, const size_t* dims)
     }
     if (d == 1) g = NdGrid{1, {0, 1, 1}};
     s->grid = g;
+    ++s->rule_gen;
     destroy_graph(s);
     return FQNM_OK;
 }

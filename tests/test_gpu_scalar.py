@@ -112,6 +112,39 @@ def test_closed_forms_found_and_verified(orc):
         s.close()
 
 
+def test_rule_reused_only_for_the_same_range_and_settings(orc):
+    """A load whose state range and settings match the last rule built keeps
+    that rule; another range, or an option set in between, builds afresh.
+    Every run gives the oracle's states."""
+    p = I.burgers_problem(n=1 << 12, steps=0)
+    q0 = gpu_q0(p)
+    want = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 150, alpha=p.alpha)
+    s = F.Solver.for_problem(p)
+    s.load(q0).step(150)
+    r1 = s.rule()
+    assert np.array_equal(s.state().astype(np.int64), want)
+    s.load(q0).step(150)                                  # same range: rule kept
+    assert s.rule() == r1
+    assert np.array_equal(s.state().astype(np.int64), want)
+    q1 = q0 + 3000                                        # shifted range: rebuilt
+    want1 = orc.step(q1, p.flux, p.delta, p.dx, p.dt, 150, alpha=p.alpha)
+    s.load(q1).step(150)
+    assert s.rule()["lo"] == r1["lo"] + 3000
+    assert np.array_equal(s.state().astype(np.int64), want1)
+    s.close()
+    # a closed form, then the same state with closed forms off, then on again
+    p = I.linear_advection_problem()
+    q0 = gpu_q0(p)
+    want = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 50, a=p.a)
+    s = F.Solver.for_problem(p)
+    for closed, evaluator in ((1, 2), (0, 1), (1, 2)):
+        F.fqnm_set_option(s.h, F.OPTION["closed_form"], closed)
+        s.load(q0).step(50)
+        assert s.rule()["evaluator"] == evaluator
+        assert np.array_equal(s.state().astype(np.int64), want)
+    s.close()
+
+
 def test_monotonicity_certificate(orc):
     s = F.Solver.for_problem(I.high_frequency_problem(n=1 << 12, steps=10))
     s.load(gpu_q0(I.high_frequency_problem(n=1 << 12, steps=10)))
