@@ -138,7 +138,7 @@ def test_rule_reused_only_for_the_same_range_and_settings(orc):
     want = orc.step(q0, p.flux, p.delta, p.dx, p.dt, 50, a=p.a)
     s = F.Solver.for_problem(p)
     for closed, evaluator in ((1, 2), (0, 1), (1, 2)):
-        F.fqnm_set_option(s.h, F.OPTION["closed_form"], closed)
+        F.fqnm_set_option(s.h, "closed_form", closed)
         s.load(q0).step(50)
         assert s.rule()["evaluator"] == evaluator
         assert np.array_equal(s.state().astype(np.int64), want)
