@@ -237,7 +237,9 @@ fqnm_status fqnm_load_states_device(fqnm_solver* s, const void* q,
 /* Quantise a double field u ([nvars][n], host or device pointer) on the GPU
  * with the flux's rounding (eq. quantisation, per-variable delta) and load
  * it as the initial state, exactly as fqnm_load_states would load the
- * quantised integers. */
+ * quantised integers.  A host field passes through a device staging buffer
+ * of nvars*n doubles that the handle keeps (shared with fqnm_observe) until
+ * fqnm_destroy. */
 fqnm_status fqnm_load_field(fqnm_solver* s, const double* u, size_t n_cells,
                             int on_device);
 
@@ -248,8 +250,9 @@ fqnm_status fqnm_step(fqnm_solver* s, uint64_t k);
 fqnm_status fqnm_sync(fqnm_solver* s);
 
 /* Observable u = delta*q (eq. reconstruction_operator) as double, [nvars][n].
- * fqnm_observe writes a host buffer and synchronises; _device writes a device
- * buffer (fp32 != 0: float) asynchronously. */
+ * fqnm_observe writes a host buffer (through the handle's staging buffer)
+ * and synchronises; _device writes a device buffer (fp32 != 0: float)
+ * asynchronously. */
 fqnm_status fqnm_observe(fqnm_solver* s, double* u_out);
 fqnm_status fqnm_observe_device(fqnm_solver* s, void* u_out, int fp32);
 
