@@ -142,9 +142,10 @@ k_march2d(const int* __restrict__ qin, int* __restrict__ qout, long long nx, lon
 // update; lanes 0 and 31 supply the x neighbours by shuffle), and each lane
 // also evaluates the row below and the row above its R rows, so the y
 // neighbours stay in the thread.  No shared memory and no barrier: the warps
-// are independent.  While slab z is updated, slab z+2's maps are evaluated
-// and slab z+3's states loaded, so two slabs of loads and gathers are in
-// flight per warp.  The update is summed in int32: the rule build checks
+// are independent.  Slab z+3's states are loaded and slab z+2's maps
+// gathered before slab z is updated, so their latency overlaps the update
+// (the slabs then shift down one register set).  The update is summed in
+// int32: the rule build checks
 // that one d-D step from inside the table's range cannot overflow, and a
 // state outside that range is a range error anyway (its maps are clamped).
 constexpr int STREAM_OWN = 30;
